@@ -1,0 +1,158 @@
+/*
+ * apsp_fw.h - C ABI of the GB300 (sm_103a) Floyd-Warshall all-pairs shortest
+ * paths library (libapspfw.so).
+ *
+ * Method: Costanzo et al., "Comparison of HPC Architectures for Computing
+ * All-Pairs Shortest Paths. Intel Xeon Phi KNL vs NVIDIA Pascal"
+ * (arXiv 2105.07298), §2.2: Floyd-Warshall (Algorithm 1) computed by blocks
+ * (the blocked FW of §2.2, "Blocked FW Algorithm": TB x TB blocks, R = N/TB
+ * rounds of four dependency-ordered phases) and §3.2 (one kernel for phase 1,
+ * one for phases 2+3, one for phase 4 per round).
+ *
+ * Common conventions
+ * ------------------
+ *  - Matrices are dense, row-major, with leading dimension ld >= n (elements):
+ *    element (i, j) is at ptr[i * ld + j].  Columns n..ld-1 are never read or
+ *    written.
+ *  - Input distances = edge weights: D[i][j] is the weight of the directed
+ *    edge i -> j, +INFINITY where there is no edge, 0 on the diagonal.  The
+ *    library does not force the diagonal.  Negative weights are allowed as
+ *    long as there is no negative cycle.  NaN gives undefined results.
+ *  - Relaxation rule (Algorithm 1, read with a strict "<"): for every k,
+ *    D[i][j] <- D[i][k] + D[k][j] when that sum is strictly smaller; the path
+ *    matrix then records P[i][j] = k (global vertex index, int32).
+ *    P[i][j] = -1 means "no intermediate vertex": the direct edge, i == j, or
+ *    no path.  path(i,j) = path(i,P[i][j]) ++ path(P[i][j],j).
+ *  - Device pointers are CUDA device (or managed) memory owned by the caller.
+ *    The library never frees or retains them after the call returns.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously; argument errors are returned at once,
+ *    before anything is enqueued; launch errors are returned as APSP_ECUDA.
+ *  - Every entry point returns an apsp_status (int).
+ *  - Results: on integer-valued weights every sum is exact (|D| < 2^24 in
+ *    FP32, < 2^53 in FP64), so D is bit-exact with any correct algorithm.
+ *    On real weights D and P are bit-exact with a sequential blocked FW of
+ *    the same block size (apsp_fw_block_size) on the same precision.
+ */
+#ifndef APSP_FW_H
+#define APSP_FW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  APSP_OK = 0,
+  APSP_EINVAL = 1,        /* bad argument (null pointer, n < 0, ld < n, ...) */
+  APSP_ECUDA = 2,         /* a CUDA call or launch failed */
+  APSP_ENOMEM = 3,        /* device scratch allocation failed */
+  APSP_EUNSUPPORTED = 4,  /* size or feature outside what this build supports */
+  APSP_ETOODEEP = 5       /* backward: a path's recursion exceeded the walk stack */
+} apsp_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *apsp_status_string(int status);
+
+/* Library version as an integer MAJOR*10000 + MINOR*100 + PATCH. */
+int apsp_version(void);
+
+/* Block edge TB used by the single-graph kernels for a precision
+ * (elem_bytes = 4 for FP32, 8 for FP64), or 0 if unsupported.  The blocked
+ * schedule (and therefore the exact rounding of real-valued sums and the
+ * tie-breaking of P) depends on TB. */
+int apsp_fw_block_size(int elem_bytes);
+
+/* ------------------------------------------------------------------------
+ * Single graph, blocked Floyd-Warshall (§2.2 "Blocked FW Algorithm";
+ * Algorithm 1 inside each block; kernels as in §3.2).
+ *
+ *   d_dist : n x n (leading dim ld) distances, overwritten in place:
+ *            input = edge weights, output = shortest-path distances.
+ *   n      : number of vertices, 0 <= n <= 65536 (n = 0 is a no-op).
+ *   ld     : leading dimension in elements, ld >= max(n, 1).
+ *   d_path : optional n x n int32 path matrix with the same ld; when non-NULL
+ *            it is fully written (P as described above).  May be NULL.
+ *   stream : cudaStream_t as void*.
+ * Returns APSP_OK, APSP_EINVAL (null d_dist with n > 0, ld < n, n > 65536)
+ * or APSP_ECUDA.
+ * ---------------------------------------------------------------------- */
+int apsp_fw_f32(float *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
+int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched Floyd-Warshall (extension of the method; the paper has no batched
+ * form): many independent graphs of uneven size in ONE persistent kernel
+ * launch.  Graph g has n_g vertices and occupies n_g * n_g consecutive
+ * elements (row-major, ld = n_g) starting at element offset off[g] of the
+ * packed buffers.  Every graph is solved with the same relaxation rule as
+ * above; results are bit-exact with the single-graph path on integer weights
+ * (and with a blocked FW of the block size of the graph's size class on real
+ * weights).
+ *
+ * Planning splits the graphs into size classes, orders them largest first
+ * (longest-processing-time order) and uploads the work list.  A plan holds
+ * device memory; it can be reused for any buffers with the same layout, and
+ * apsp_fw_batched_run_f32 enqueues exactly one memset and one kernel launch,
+ * so it can be captured in a CUDA graph.
+ *
+ *   h_n, h_off : HOST arrays, num_graphs entries: vertex counts (1..1024)
+ *                and element offsets (each a multiple of 4, i.e. 16-byte
+ *                aligned for FP32 / int32).
+ *   d_dist     : packed FP32 distances, overwritten in place.
+ *   d_path     : packed int32 path matrices (same offsets), or NULL.
+ * apsp_fw_batched_f32 = plan + run + destroy (allocates and frees its work
+ * list with stream-ordered allocation on `stream`).
+ * ---------------------------------------------------------------------- */
+typedef struct apsp_batched_plan apsp_batched_plan;
+
+int apsp_batched_plan_create(const int32_t *h_n, const int64_t *h_off, int32_t num_graphs,
+                             apsp_batched_plan **out_plan);
+int apsp_batched_plan_destroy(apsp_batched_plan *plan);
+int apsp_fw_batched_run_f32(const apsp_batched_plan *plan, float *d_dist, int32_t *d_path,
+                            void *stream);
+int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_t *h_n, const int64_t *h_off,
+                        int32_t num_graphs, void *stream);
+
+/* Autotuner hook for the batched kernel: per size class (0..3, vertex-count
+ * bounds given by apsp_batched_class_bounds) pick the variant index used by
+ * later plans.  apsp_batched_num_variants reports how many variants a class
+ * has.  Defaults are the built-in table. */
+int apsp_batched_num_classes(void);
+int apsp_batched_class_bounds(int cls, int32_t *lo, int32_t *hi);
+int apsp_batched_num_variants(int cls);
+int apsp_batched_set_variant(int cls, int variant);
+int apsp_batched_get_variant(int cls);
+
+/* ------------------------------------------------------------------------
+ * Backward pass (extension; not in the paper).  D[i][j] is the sum of the
+ * weights along path(i,j) as encoded by P, so for a loss L(D):
+ *     dL/dW[u][v] = sum over (i,j) whose path uses edge (u,v) of dL/dD[i][j].
+ * The kernel recomputes every path from P (nothing is stored by the forward
+ * pass beyond P and D) and scatters dL/dD[i][j] onto its edges.
+ *
+ *   d_grad_dist : batch x (n x n, leading dim ld) upstream gradient dL/dD.
+ *   d_path      : the path matrices P from the forward pass (same layout).
+ *   d_dist      : the forward distances D (same layout); pairs with
+ *                 D = +inf (no path) and the diagonal contribute nothing.
+ *   d_grad_w    : output dL/dW (same layout), fully written: zero on the
+ *                 diagonal, on non-edges and on edges no path uses.
+ *   n, ld       : vertices and leading dimension (ld >= n).
+ *   batch       : number of graphs, each `stride` elements after the last
+ *                 (stride >= n * ld).
+ *   d_status    : optional device int32; receives APSP_OK or APSP_ETOODEEP
+ *                 (a path whose split recursion is deeper than 256 levels,
+ *                 or a P that does not encode a path;
+ *                 its contribution is then incomplete).  May be NULL.
+ * Accumulation is FP32 atomic addition; the summation order is not fixed.
+ * ---------------------------------------------------------------------- */
+int apsp_fw_backward_f32(const float *d_grad_dist, const int32_t *d_path, const float *d_dist,
+                         float *d_grad_w, int64_t n, int64_t ld, int64_t batch, int64_t stride,
+                         int32_t *d_status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APSP_FW_H */

@@ -1,0 +1,148 @@
+"""GB300 (sm_103a) blocked Floyd-Warshall all-pairs shortest paths.
+
+A thin Python binding over the C ABI in ``include/apsp_fw.h`` (``libapspfw.so``,
+built from ``csrc/`` by :mod:`paper_2105_07298_gb300.build`).  Every function
+here only marshals arguments (device pointers, sizes, the current CUDA stream)
+and calls the library; all of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+
+Method: Costanzo et al., arXiv 2105.07298, §2.2 (Algorithm 1, blocked FW with
+four phases per round) and §3.2 (kernel split per round).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libapspfw.so")
+
+APSP_OK, APSP_EINVAL, APSP_ECUDA, APSP_ENOMEM, APSP_EUNSUPPORTED, APSP_ETOODEEP = range(6)
+
+# Every symbol include/apsp_fw.h declares, with its ctypes signature.
+_i32, _i64, _p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+SIGNATURES = {
+    "apsp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "apsp_version": (ctypes.c_int, []),
+    "apsp_fw_block_size": (ctypes.c_int, [ctypes.c_int]),
+    "apsp_fw_f32": (ctypes.c_int, [_p, _i64, _i64, _p, _p]),
+    "apsp_fw_f64": (ctypes.c_int, [_p, _i64, _i64, _p, _p]),
+    "apsp_batched_plan_create": (ctypes.c_int, [_p, _p, _i32, ctypes.POINTER(_p)]),
+    "apsp_batched_plan_destroy": (ctypes.c_int, [_p]),
+    "apsp_fw_batched_run_f32": (ctypes.c_int, [_p, _p, _p, _p]),
+    "apsp_fw_batched_f32": (ctypes.c_int, [_p, _p, _p, _p, _i32, _p]),
+    "apsp_batched_num_classes": (ctypes.c_int, []),
+    "apsp_batched_class_bounds": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "apsp_batched_num_variants": (ctypes.c_int, [ctypes.c_int]),
+    "apsp_batched_set_variant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "apsp_batched_get_variant": (ctypes.c_int, [ctypes.c_int]),
+    "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ApspError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        msg = load().apsp_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg}" if where else msg)
+
+
+def load(path: str | None = None):
+    """Load libapspfw.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                from . import build as _build
+                _build.build()
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != APSP_OK:
+        raise ApspError(status, where)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(int(s.cuda_stream))
+
+
+def _matrix_args(t, dtype):
+    """(ptr, n, ld) of an n x n row-major view with unit column stride."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError(f"expected an n x n matrix, got shape {tuple(t.shape)}")
+    n = t.shape[0]
+    if n > 1 and t.stride(1) != 1:
+        raise ValueError("columns must be contiguous (stride(1) == 1)")
+    ld = t.stride(0) if n > 1 else max(n, 1)
+    return ctypes.c_void_p(t.data_ptr()), n, ld
+
+
+def block_size(dtype) -> int:
+    """Block edge TB the single-graph kernels use for ``dtype`` (torch.float32/float64)."""
+    import torch
+    return int(load().apsp_fw_block_size(4 if dtype == torch.float32 else 8))
+
+
+def _fw(fn_name, dist, path, stream, dtype):
+    import torch
+    ptr, n, ld = _matrix_args(dist, dtype)
+    pptr = None
+    if path is not None:
+        pp, pn, pld = _matrix_args(path, torch.int32)
+        if pn != n or pld != ld or path.device != dist.device:
+            raise ValueError("path must be an int32 matrix with the same n, ld and device as dist")
+        pptr = pp
+    _check(getattr(load(), fn_name)(ptr, n, ld, pptr, _stream_ptr(stream)), fn_name)
+    return dist, path
+
+
+def apsp_fw_f32(dist, path=None, stream=None):
+    """In-place FP32 blocked Floyd-Warshall on a CUDA n x n tensor (optionally writing ``path``)."""
+    import torch
+    return _fw("apsp_fw_f32", dist, path, stream, torch.float32)
+
+
+def apsp_fw_f64(dist, path=None, stream=None):
+    """In-place FP64 blocked Floyd-Warshall on a CUDA n x n tensor (optionally writing ``path``)."""
+    import torch
+    return _fw("apsp_fw_f64", dist, path, stream, torch.float64)
+
+
+def apsp_fw(dist, path=None, stream=None):
+    """Dispatch on dtype to :func:`apsp_fw_f32` / :func:`apsp_fw_f64`."""
+    import torch
+    if dist.dtype == torch.float32:
+        return apsp_fw_f32(dist, path, stream)
+    if dist.dtype == torch.float64:
+        return apsp_fw_f64(dist, path, stream)
+    raise TypeError(f"unsupported dtype {dist.dtype}")
+
+
+from .batched import BatchedPlan, apsp_fw_batched_f32, apsp_fw_batched  # noqa: E402
+from .backward import apsp_fw_backward_f32, ShortestPathDistances, shortest_path_distances  # noqa: E402
+
+__all__ = [
+    "load", "ApspError", "block_size", "apsp_fw_f32", "apsp_fw_f64", "apsp_fw",
+    "BatchedPlan", "apsp_fw_batched_f32", "apsp_fw_batched", "apsp_fw_backward_f32",
+    "ShortestPathDistances", "shortest_path_distances",
+]

@@ -1,0 +1,259 @@
+// Batched Floyd-Warshall: thousands of independent graphs of uneven size in
+// one persistent launch (an extension; the paper solves one matrix at a time).
+//
+// Work distribution: the plan orders the graphs largest first (longest
+// processing time first) and the CTAs of a grid sized to fill every SM pop
+// graph indices from one atomic counter.  A CTA solves its graph alone, so no
+// CTA ever waits on another.
+//
+// Per graph (n_g <= 1024, row-major, ld = n_g) the CTA runs the blocked FW of
+// §2.2 with TB = 128 on the matrix in global memory (it stays in L2):
+//   phase 1     register-resident closure of the diagonal block (Algorithm 1
+//               restricted to the block, k sequential);
+//   phases 2+3  row block (r,J) <- min(C, D*(r,r) (x) C) and column block
+//               (I,r) <- min(C, C (x) D*(r,r)): once the diagonal block is
+//               closed, the sequential k loop over a panel block equals one
+//               min-plus product with the closed block, so these phases use
+//               the same register-blocked product as phase 4;
+//   phase 4     (I,J) <- min(C, D(I,r) (x) D(r,J)).
+// On integer-valued weights all sums are exact and D equals every other
+// correct FW; on real weights the phase-2/3 products round differently from
+// the sequential loop (one sum through the closed block instead of a chain of
+// sums), within the same error bound.
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "minplus_f32.cuh"
+
+namespace apsp {
+
+constexpr int kBatchedMaxN = 1024;
+
+// Size classes and their kernel variants (selected by the autotuner).  The
+// variant changes how a class's graphs are processed inside the one launch.
+//   variant 0: blocked, TB = 128 (all phases on 8 x 8 register tiles)
+constexpr int kNumClasses = 4;
+static const int32_t kClassLo[kNumClasses] = {1, 65, 129, 257};
+static const int32_t kClassHi[kNumClasses] = {64, 128, 256, kBatchedMaxN};
+constexpr int kNumVariants = 1;
+static int g_variant[kNumClasses] = {0, 0, 0, 0};
+
+union BatchedSmem {
+  mp32::Smem prod;
+  mp32::DiagSmem diag;
+};
+
+__device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *__restrict__ P,
+                                                int n, BatchedSmem &sm) {
+  using mp32::T;
+  const int ld = n;
+  const int vec_ok = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
+  if (P) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[e] = -1;
+  }
+  __syncthreads();
+  const int R = (n + T - 1) / T;
+  for (int r = 0; r < R; ++r) {
+    const int base = r * T, m = min(T, n - base);
+    mp32::diag_closure(D, ld, P, base, m, sm.diag);
+    __syncthreads();
+    for (int J = 0; J < R; ++J) {
+      if (J == r) continue;
+      mp32::block_product(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, vec_ok, sm.prod);
+    }
+    for (int I = 0; I < R; ++I) {
+      if (I == r) continue;
+      mp32::block_product(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, vec_ok, sm.prod);
+    }
+    __syncthreads();
+    for (int I = 0; I < R; ++I) {
+      if (I == r) continue;
+      for (int J = 0; J < R; ++J) {
+        if (J == r) continue;
+        mp32::block_product(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m,
+                            vec_ok, sm.prod);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(mp32::THREADS, 2)
+    fw_batched_persistent_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
+                              const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
+                              const int64_t *__restrict__ offs, int num, int *__restrict__ counter) {
+  __shared__ __align__(16) BatchedSmem sm;
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_next;
+    __syncthreads();  // all threads have read s_next before it is overwritten
+    if (t >= num) break;
+    const int g = order[t];
+    const int64_t off = offs[g];
+    solve_graph_f32(Dp + off, Pp ? Pp + off : nullptr, ns[g], sm);
+  }
+}
+
+}  // namespace apsp
+
+struct apsp_batched_plan {
+  int32_t num;
+  int32_t *d_order;
+  int32_t *d_n;
+  int64_t *d_off;
+  int *d_counter;
+  int grid;
+};
+
+namespace {
+
+int validate(const int32_t *h_n, const int64_t *h_off, int32_t num) {
+  if (num < 0 || (num > 0 && (!h_n || !h_off))) return APSP_EINVAL;
+  for (int32_t g = 0; g < num; ++g) {
+    if (h_n[g] < 1 || h_n[g] > apsp::kBatchedMaxN) return h_n[g] < 1 ? APSP_EINVAL : APSP_EUNSUPPORTED;
+    if (h_off[g] < 0 || (h_off[g] & 3)) return APSP_EINVAL;
+  }
+  return APSP_OK;
+}
+
+std::vector<int32_t> lpt_order(const int32_t *h_n, int32_t num) {
+  std::vector<int32_t> order(num);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return h_n[a] > h_n[b]; });
+  return order;
+}
+
+int grid_for(int32_t num) {
+  int dev = 0, sms = 0, occ = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apsp::fw_batched_persistent_f32,
+                                                    apsp::mp32::THREADS, 0) != cudaSuccess)
+    return -1;
+  const int g = sms * std::max(occ, 1);
+  return std::max(1, std::min<int>(g, num));
+}
+
+}  // namespace
+
+APSP_EXPORT int apsp_batched_plan_create(const int32_t *h_n, const int64_t *h_off, int32_t num,
+                                         apsp_batched_plan **out_plan) {
+  if (!out_plan) return APSP_EINVAL;
+  *out_plan = nullptr;
+  int st = validate(h_n, h_off, num);
+  if (st) return st;
+  apsp_batched_plan *p = (apsp_batched_plan *)calloc(1, sizeof(apsp_batched_plan));
+  if (!p) return APSP_ENOMEM;
+  p->num = num;
+  const size_t cnt = (size_t)std::max(num, 1);
+  if (cudaMalloc(&p->d_order, cnt * 4) != cudaSuccess || cudaMalloc(&p->d_n, cnt * 4) != cudaSuccess ||
+      cudaMalloc(&p->d_off, cnt * 8) != cudaSuccess || cudaMalloc(&p->d_counter, 4) != cudaSuccess) {
+    apsp_batched_plan_destroy(p);
+    return APSP_ENOMEM;
+  }
+  if (num > 0) {
+    std::vector<int32_t> order = lpt_order(h_n, num);
+    if (cudaMemcpy(p->d_order, order.data(), (size_t)num * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+      apsp_batched_plan_destroy(p);
+      return APSP_ECUDA;
+    }
+  }
+  p->grid = grid_for(num);
+  if (p->grid < 0) {
+    apsp_batched_plan_destroy(p);
+    return APSP_ECUDA;
+  }
+  *out_plan = p;
+  return APSP_OK;
+}
+
+APSP_EXPORT int apsp_batched_plan_destroy(apsp_batched_plan *p) {
+  if (!p) return APSP_OK;
+  cudaFree(p->d_order);
+  cudaFree(p->d_n);
+  cudaFree(p->d_off);
+  cudaFree(p->d_counter);
+  free(p);
+  return APSP_OK;
+}
+
+APSP_EXPORT int apsp_fw_batched_run_f32(const apsp_batched_plan *p, float *d_dist, int32_t *d_path,
+                                        void *stream) {
+  if (!p) return APSP_EINVAL;
+  if (p->num == 0) return APSP_OK;
+  if (!d_dist) return APSP_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) return APSP_ECUDA;
+  apsp::fw_batched_persistent_f32<<<p->grid, apsp::mp32::THREADS, 0, s>>>(
+      d_dist, d_path, p->d_order, p->d_n, p->d_off, p->num, p->d_counter);
+  return apsp::status_from(cudaGetLastError());
+}
+
+APSP_EXPORT int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_t *h_n,
+                                    const int64_t *h_off, int32_t num, void *stream) {
+  int st = validate(h_n, h_off, num);
+  if (st) return st;
+  if (num == 0) return APSP_OK;
+  if (!d_dist) return APSP_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<int32_t> order = lpt_order(h_n, num);
+  // one scratch block: counter | order | n | offsets (stream-ordered allocation)
+  const size_t bytes = 16 + (size_t)num * 8 + (size_t)num * 8 + (size_t)num * 8;
+  char *scratch = nullptr;
+  cudaGetLastError();
+  if (cudaMallocAsync((void **)&scratch, bytes, s) != cudaSuccess) return APSP_ENOMEM;
+  int *d_counter = reinterpret_cast<int *>(scratch);
+  int32_t *d_order = reinterpret_cast<int32_t *>(scratch + 16);
+  int32_t *d_n = d_order + num;
+  int64_t *d_off = reinterpret_cast<int64_t *>(scratch + 16 + (((size_t)num * 8 + 15) & ~(size_t)15));
+  // offsets region starts 16-byte aligned after order and n (2 * 4 * num bytes)
+  cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order.data(), (size_t)num * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice, s);
+  int grid = grid_for(num);
+  if (e == cudaSuccess && grid > 0) {
+    apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, 0, s>>>(d_dist, d_path, d_order, d_n,
+                                                                          d_off, num, d_counter);
+    e = cudaGetLastError();
+  }
+  // Copies from pageable host memory have consumed their sources when they
+  // return, so `order` may go out of scope; the scratch is freed in stream order.
+  cudaFreeAsync(scratch, s);
+  if (grid <= 0) return APSP_ECUDA;
+  return apsp::status_from(e);
+}
+
+APSP_EXPORT int apsp_batched_num_classes(void) { return apsp::kNumClasses; }
+
+APSP_EXPORT int apsp_batched_class_bounds(int cls, int32_t *lo, int32_t *hi) {
+  if (cls < 0 || cls >= apsp::kNumClasses || !lo || !hi) return APSP_EINVAL;
+  *lo = apsp::kClassLo[cls];
+  *hi = apsp::kClassHi[cls];
+  return APSP_OK;
+}
+
+APSP_EXPORT int apsp_batched_num_variants(int cls) {
+  return (cls < 0 || cls >= apsp::kNumClasses) ? 0 : apsp::kNumVariants;
+}
+
+APSP_EXPORT int apsp_batched_set_variant(int cls, int variant) {
+  if (cls < 0 || cls >= apsp::kNumClasses || variant < 0 || variant >= apsp::kNumVariants)
+    return APSP_EINVAL;
+  apsp::g_variant[cls] = variant;
+  return APSP_OK;
+}
+
+APSP_EXPORT int apsp_batched_get_variant(int cls) {
+  return (cls < 0 || cls >= apsp::kNumClasses) ? -1 : apsp::g_variant[cls];
+}

@@ -1,0 +1,62 @@
+"""CPU-side checks of the boundary: the library builds for sm_103a, loads, and
+exports every symbol include/apsp_fw.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2105_07298_gb300 as apsp
+from paper_2105_07298_gb300 import build as apsp_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "apsp_fw.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(apsp_\w+)\s*\(", txt)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == sorted(apsp.SIGNATURES)
+
+
+def test_library_builds_loads_and_exports():
+    path = apsp_build.build()
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    L = apsp.load()
+    assert L.apsp_version() >= 100
+    assert L.apsp_fw_block_size(4) == 128 and L.apsp_fw_block_size(8) == 64
+    assert L.apsp_fw_block_size(2) == 0
+    assert L.apsp_status_string(0) == b"APSP_OK"
+    assert L.apsp_batched_num_classes() == 4
+    lo, hi = ctypes.c_int32(), ctypes.c_int32()
+    assert L.apsp_batched_class_bounds(3, ctypes.byref(lo), ctypes.byref(hi)) == 0 and hi.value == 1024
+
+
+def test_only_sm103a_code_in_build_flags():
+    assert apsp_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_product_does_not_import_oracle():
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2105_07298_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b", src.replace("oracle's", "")) or f.endswith(".md"), f
+
+
+def test_argument_errors_without_gpu():
+    """Argument checks return before any CUDA call."""
+    L = apsp.load()
+    assert L.apsp_fw_f32(None, 5, 5, None, None) == 1
+    assert L.apsp_fw_f64(None, 5, 4, None, None) == 1
+    assert L.apsp_fw_f32(None, 0, 0, None, None) == 0
+    plan = ctypes.c_void_p()
+    n = (ctypes.c_int32 * 1)(2000)
+    off = (ctypes.c_int64 * 1)(0)
+    assert L.apsp_batched_plan_create(n, off, 1, ctypes.byref(plan)) == 4
+    assert L.apsp_batched_plan_create(None, None, 1, ctypes.byref(plan)) == 1

@@ -1,0 +1,115 @@
+"""GPU parity of the batched persistent kernel against the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+import paper_2105_07298_gb300 as apsp
+from paper_2105_07298_gb300 import batched as B
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _pack(mats, off, total):
+    buf = np.full(total, np.nan, dtype=np.float32)
+    for m, o in zip(mats, off):
+        buf[o:o + m.size] = m.reshape(-1)
+    return buf
+
+
+def _solve(sizes, mats, with_path=True, plan=True):
+    off = B.packed_offsets(sizes)
+    total = B.packed_numel(sizes)
+    d = torch.from_numpy(_pack(mats, off, total)).to(DEV)
+    p = torch.full((total,), 777, dtype=torch.int32, device=DEV) if with_path else None
+    if plan:
+        pl = B.BatchedPlan(sizes, off)
+        pl.run(d, p)
+        pl.close()
+    else:
+        B.apsp_fw_batched_f32(d, sizes, off, p)
+    torch.cuda.synchronize()
+    dh = d.cpu().numpy()
+    ph = p.cpu().numpy() if p is not None else None
+    out = []
+    for n, o in zip(sizes, off):
+        n = int(n)
+        out.append((dh[o:o + n * n].reshape(n, n),
+                    ph[o:o + n * n].reshape(n, n) if ph is not None else None))
+    return out
+
+
+@pytest.mark.parametrize("use_plan", [True, False])
+def test_uneven_batch_integer_exact(use_plan):
+    sizes = [1, 2, 5, 16, 33, 64, 65, 100, 127, 128, 129, 200, 256, 257, 300, 383, 384, 385, 512]
+    mats = [graphgen.dense_graph(n, 0.3, 500 + g) for g, n in enumerate(sizes)]
+    res = _solve(sizes, mats, plan=use_plan)
+    for W, (D, P) in zip(mats, res):
+        np.testing.assert_array_equal(D, oracle.fw(W)[0])
+        assert oracle.check_paths(W, D, P) == 0
+
+
+def test_batch_real_weights_tolerance():
+    sizes = [50, 130, 260]
+    mats = [graphgen.dense_graph(n, 0.4, 900 + n, weights="real", lo=0.5, hi=2.0) for n in sizes]
+    for W, (D, P) in zip(mats, _solve(sizes, mats)):
+        D64 = oracle.fw(W.astype(np.float64))[0]
+        fin = np.isfinite(D64)
+        np.testing.assert_array_equal(np.isfinite(D), fin)
+        np.testing.assert_allclose(D[fin], D64[fin], rtol=1e-5)
+        assert oracle.check_paths(W, D, P, rtol=1e-5) == 0
+
+
+def test_batch_without_path_and_edge_cases():
+    sizes = [3, 1, 1024]
+    mats = [graphgen.dense_graph(n, 0.3, 40 + n) for n in sizes]
+    for W, (D, _) in zip(mats, _solve(sizes, mats, with_path=False)):
+        np.testing.assert_array_equal(D, oracle.fw(W)[0])
+    # empty batch is a no-op; sizes beyond the supported maximum are rejected
+    B.BatchedPlan([], []).close()
+    with pytest.raises(apsp.ApspError):
+        B.BatchedPlan([1025], [0])
+    with pytest.raises(apsp.ApspError):
+        B.BatchedPlan([0], [0])
+    with pytest.raises(apsp.ApspError):
+        B.BatchedPlan([4], [2])  # offset not a multiple of 4 elements
+
+
+def test_batch_matches_single_graph_path():
+    sizes = [96, 250, 130]
+    mats = [graphgen.dense_graph(n, 0.3, 60 + n) for n in sizes]
+    res = _solve(sizes, mats)
+    for W, (D, _) in zip(mats, res):
+        t = torch.from_numpy(W).to(DEV)
+        apsp.apsp_fw_f32(t)
+        np.testing.assert_array_equal(D, t.cpu().numpy())
+
+
+def test_full_config_sampled_graphs():
+    """4096 graphs, n uniform on [16, 512], edge probability 0.3, integer weights:
+    one launch; 24 sampled graphs checked against the oracle."""
+    sizes = graphgen.batch_sizes(4096, 16, 512, 1)
+    off = B.packed_offsets(sizes)
+    total = B.packed_numel(sizes)
+    buf = np.empty(total, dtype=np.float32)
+    for g, n in enumerate(sizes):
+        buf[off[g]:off[g] + n * n] = graphgen.dense_graph(int(n), 0.3, 1 * 1000003 + g).reshape(-1)
+    d = torch.from_numpy(buf).to(DEV)
+    p = torch.empty(total, dtype=torch.int32, device=DEV)
+    plan = B.BatchedPlan(sizes, off)
+    plan.run(d, p)
+    torch.cuda.synchronize()
+    dh, ph = d.cpu().numpy(), p.cpu().numpy()
+    rng = np.random.default_rng(7)
+    picks = list(rng.choice(4096, 22, replace=False)) + [int(np.argmax(sizes)), int(np.argmin(sizes))]
+    for g in picks:
+        n = int(sizes[g])
+        W = buf[off[g]:off[g] + n * n].reshape(n, n)
+        D = dh[off[g]:off[g] + n * n].reshape(n, n)
+        P = ph[off[g]:off[g] + n * n].reshape(n, n)
+        np.testing.assert_array_equal(D, oracle.fw(W)[0])
+        pairs = list(zip(rng.integers(0, n, 300).tolist(), rng.integers(0, n, 300).tolist()))
+        assert oracle.check_paths(W, D, P, pairs=pairs) == 0
+    plan.close()

@@ -1,0 +1,185 @@
+"""GPU parity: the CUDA blocked FW (through the C ABI) against the CPU oracle.
+
+Inputs come from graphgen (seeded); expected values only from ``oracle``.
+Bars (the readings behind them are in the oracle's header):
+  * integer weights: D bit-exact with classic FW (every sum is exact);
+  * real weights: D and P bit-exact with the oracle's blocked FW at the
+    library's block size in the same precision (same candidate sums, same
+    ascending-k strict-"<" tie rule), and within 1e-5 (FP32) / 1e-12 (FP64)
+    relative of an FP64 classic FW;
+  * P: every path rebuilt from it is made of existing edges and weighs D.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+import paper_2105_07298_gb300 as apsp
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _run(W, dtype, with_path=True, ld=None):
+    n = W.shape[0]
+    ld = ld or n
+    tdt = torch.float32 if dtype == np.float32 else torch.float64
+    buf = torch.full((max(n, 1), max(ld, 1)), float("nan"), dtype=tdt, device=DEV)
+    D = buf[:n, :n] if n else buf[:0, :0]
+    D.copy_(torch.from_numpy(np.ascontiguousarray(W, dtype=dtype)))
+    P = None
+    if with_path:
+        pbuf = torch.full((max(n, 1), max(ld, 1)), 12345, dtype=torch.int32, device=DEV)
+        P = pbuf[:n, :n]
+    apsp.apsp_fw(D, P)
+    torch.cuda.synchronize()
+    pad_ok = bool(torch.isnan(buf[:n, n:ld]).all()) if ld > n else True
+    return D.cpu().numpy(), (P.cpu().numpy() if P is not None else None), pad_ok
+
+
+def _sample_pairs(n, count, seed):
+    rng = np.random.default_rng(seed)
+    return list(zip(rng.integers(0, n, count).tolist(), rng.integers(0, n, count).tolist()))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 64, 65, 127, 128, 129, 200, 255, 257, 300])
+def test_integer_weights_bit_exact(n, dtype):
+    W = graphgen.dense_graph(n, 0.3, 1000 + n, dtype=dtype)
+    D, P, _ = _run(W, dtype)
+    Dref, _ = oracle.fw(W.astype(np.float64))
+    np.testing.assert_array_equal(D.astype(np.float64), Dref)
+    assert oracle.check_paths(W, D, P) == 0
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [70, 200, 333])
+def test_real_weights_match_blocked_oracle_bitwise(n, dtype):
+    W = graphgen.dense_graph(n, 0.4, 77 + n, weights="real", lo=0.5, hi=2.0, dtype=dtype)
+    D, P, _ = _run(W, dtype)
+    TB = apsp.block_size(torch.float32 if dtype == np.float32 else torch.float64)
+    Db, Pb = oracle.bfw(W, TB)
+    np.testing.assert_array_equal(D, Db)
+    np.testing.assert_array_equal(P, Pb)
+    # and against the exact (FP64 classic) distances
+    D64, _ = oracle.fw(W.astype(np.float64))
+    fin = np.isfinite(D64)
+    np.testing.assert_array_equal(np.isfinite(D), fin)
+    rel = np.abs(D[fin].astype(np.float64) - D64[fin]) / np.maximum(np.abs(D64[fin]), 1e-300)
+    assert rel.max() <= (1e-5 if dtype == np.float32 else 1e-12), rel.max()
+    assert oracle.check_paths(W, D, P, rtol=1e-5 if dtype == np.float32 else 1e-12) == 0
+
+
+def test_config_small_n1024_full():
+    """n = 1024, edge probability 0.3, integer weights [1, 100], FP32 + int32 path."""
+    W = graphgen.dense_graph(1024, 0.3, 1)
+    D, P, _ = _run(W, np.float32)
+    Dref, Pref = oracle.fw(W)
+    np.testing.assert_array_equal(D, Dref)
+    assert oracle.check_paths(W, D, P, pairs=_sample_pairs(1024, 4000, 3)) == 0
+    # blocked oracle at the library's block size: identical P as well
+    Db, Pb = oracle.bfw(W, apsp.block_size(torch.float32))
+    np.testing.assert_array_equal(P, Pb)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_n2048_full_bit_exact(dtype):
+    W = graphgen.dense_graph(2048, 0.5, 2048, dtype=dtype)
+    D, P, _ = _run(W, dtype)
+    Dref, _ = oracle.fw(W.astype(np.float64))
+    np.testing.assert_array_equal(D.astype(np.float64), Dref)
+    assert oracle.check_paths(W, D, P, pairs=_sample_pairs(2048, 3000, 4)) == 0
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_leading_dimension_and_padding(dtype):
+    """ld > n (aligned and unaligned): padding columns are never touched."""
+    for n, ld in ((130, 136), (130, 131), (257, 259)):
+        W = graphgen.dense_graph(n, 0.3, n * 7 + ld, dtype=dtype)
+        D, P, pad_ok = _run(W, dtype, ld=ld)
+        assert pad_ok
+        Dref, _ = oracle.fw(W.astype(np.float64))
+        np.testing.assert_array_equal(D.astype(np.float64), Dref)
+        assert oracle.check_paths(W, D, P) == 0
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_without_path_matrix(dtype):
+    W = graphgen.dense_graph(300, 0.3, 9, dtype=dtype)
+    D, _, _ = _run(W, dtype, with_path=False)
+    np.testing.assert_array_equal(D.astype(np.float64), oracle.fw(W.astype(np.float64))[0])
+
+
+def test_structured_graphs():
+    # chain across several blocks, grid, disconnected halves, negative weights via potentials
+    W = graphgen.chain_graph(np.arange(1, 300, dtype=np.float64) % 7 + 1).astype(np.float32)
+    D, P, _ = _run(W, np.float32)
+    np.testing.assert_array_equal(D, oracle.fw(W)[0])
+    assert oracle.check_paths(W, D, P, pairs=_sample_pairs(300, 500, 1)) == 0
+    G = graphgen.grid_graph(13, 17).astype(np.float32)
+    D, P, _ = _run(G, np.float32)
+    np.testing.assert_array_equal(D, oracle.fw(G)[0])
+    A = graphgen.dense_graph(150, 0.2, 5)
+    Wd = np.full((300, 300), np.inf, dtype=np.float32)
+    Wd[:150, :150] = A
+    Wd[150:, 150:] = A
+    D, P, _ = _run(Wd, np.float32)
+    assert np.isinf(D[:150, 150:]).all() and (P[:150, 150:] == -1).all()
+    h = np.random.default_rng(3).integers(-40, 40, 260).astype(np.float64)
+    W0 = graphgen.dense_graph(260, 0.3, 6, dtype=np.float64)
+    Wn = np.where(np.isfinite(W0), W0 + h[:, None] - h[None, :], np.inf)
+    np.fill_diagonal(Wn, 0)
+    for dt in (np.float32, np.float64):
+        D, P, _ = _run(Wn.astype(dt), dt)
+        np.testing.assert_array_equal(D.astype(np.float64), oracle.fw(Wn)[0])
+
+
+def test_argument_errors():
+    lib = apsp.load()
+    x = torch.zeros((4, 4), device=DEV)
+    assert lib.apsp_fw_f32(None, 4, 4, None, None) == apsp.APSP_EINVAL
+    assert lib.apsp_fw_f32(x.data_ptr(), 4, 3, None, None) == apsp.APSP_EINVAL
+    assert lib.apsp_fw_f32(x.data_ptr(), -1, 4, None, None) == apsp.APSP_EINVAL
+    assert lib.apsp_fw_f32(x.data_ptr(), 70000, 70000, None, None) == apsp.APSP_EINVAL
+    assert lib.apsp_fw_f32(None, 0, 0, None, None) == apsp.APSP_OK  # empty graph: no-op
+    with pytest.raises(ValueError):
+        apsp.apsp_fw_f32(x.t())  # columns not contiguous
+    with pytest.raises(TypeError):
+        apsp.apsp_fw_f32(x.double())
+
+
+def _dijkstra_check(D_dev, W_host, srcs):
+    ref = oracle.dijkstra_rows(W_host, srcs)
+    got = D_dev[torch.as_tensor(srcs, device=D_dev.device)].double().cpu().numpy()
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("n,dtype", [(16384, torch.float32), (16384, torch.float64),
+                                     (32768, torch.float32)])
+def test_full_size_sampled_rows(n, dtype):
+    """Full-size blocked FW (edge probability 0.5, integer weights): sampled
+    rows against Dijkstra (exact) and sampled paths against the weights."""
+    W = graphgen.dense_graph_torch(n, 0.5, 20210517, dtype=dtype, device=DEV)
+    W_host = W.cpu().numpy()
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.apsp_fw(W, P)
+    torch.cuda.synchronize()
+    srcs = np.random.default_rng(n).integers(0, n, 8)
+    _dijkstra_check(W, W_host, srcs)
+    # path validation on sampled pairs, reading rows of P and D on demand
+    rows = sorted(set(srcs.tolist()))
+    pairs = [(int(i), int(j)) for i in rows for j in np.random.default_rng(int(i)).integers(0, n, 40)]
+    Ph = P.cpu().numpy()
+    Dh = W[torch.as_tensor(rows, device=DEV)].double().cpu().numpy()
+    dmap = {r: Dh[t] for t, r in enumerate(rows)}
+    bad = 0
+    for i, j in pairs:
+        path = oracle.reconstruct_path(Ph, i, j)
+        if i == j:
+            continue
+        s = 0.0
+        for a, b in zip(path[:-1], path[1:]):
+            s += float(W_host[a, b])
+        bad += int(s != dmap[i][j])
+    assert bad == 0
