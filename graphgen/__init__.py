@@ -223,3 +223,57 @@ def random_tree_graph(n: int, seed: int, lo=0.5, hi=2.0, dtype=np.float64) -> tu
         parent[v] = rng.integers(0, v)
         W[parent[v], v] = rng.uniform(lo, hi)
     return W, parent
+
+
+def batched_graphs_torch(sizes, p: float, seed: int, offsets, total: int, *, weights: str = "int",
+                         lo: float = 1, hi: float = 100, device="cpu", dtype=None):
+    """All graphs of :func:`batched_graphs` drawn at once with torch into one packed
+    buffer of ``total`` elements (graph g at element offsets[g]); element values are
+    identical to the numpy draw (same per-graph seeds and hashes)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    sizes = np.asarray(sizes, dtype=np.int64)
+    out = torch.full((total,), float("nan"), dtype=dtype, device=device)
+    if len(sizes) == 0:
+        return out
+    keys = np.array([stream_keys(seed * 1000003 + g) for g in range(len(sizes))], dtype=np.int64)
+    thr = min(int(round(p * 2.0 ** 32)), 1 << 32)
+    M = torch.tensor(_M32, dtype=torch.int64, device=device)
+
+    def fmix(h):
+        h = h & M
+        h = h ^ (h >> 16)
+        h = (h * _C1) & M
+        h = h ^ (h >> 13)
+        h = (h * _C2) & M
+        h = h ^ (h >> 16)
+        return h
+
+    # process graphs in groups to bound temporaries
+    g0 = 0
+    while g0 < len(sizes):
+        g1 = g0
+        acc = 0
+        while g1 < len(sizes) and (acc == 0 or acc + sizes[g1] ** 2 <= (1 << 26)):
+            acc += int(sizes[g1]) ** 2
+            g1 += 1
+        cnt = torch.as_tensor(sizes[g0:g1] ** 2, device=device)
+        gid = torch.repeat_interleave(torch.arange(g0, g1, device=device), cnt)
+        start = torch.cumsum(cnt, 0) - cnt
+        e = torch.arange(acc, device=device) - torch.repeat_interleave(start, cnt)  # local index i*n+j
+        ke = torch.as_tensor(keys[g0:g1, 0], device=device)[gid - g0]
+        kw = torch.as_tensor(keys[g0:g1, 1], device=device)[gid - g0]
+        he = fmix(e ^ ke)
+        hw = fmix(e ^ kw)
+        if weights == "int":
+            w = float(lo) + (hw % (int(hi) - int(lo) + 1)).to(torch.float64)
+        else:
+            w = float(lo) + (float(hi) - float(lo)) * (hw.to(torch.float64) / 2.0 ** 32)
+        w = torch.where(he < thr, w, torch.full_like(w, float("inf")))
+        nn = torch.as_tensor(sizes[g0:g1], device=device)[gid - g0]
+        w = torch.where((e // nn) == (e % nn), torch.zeros_like(w), w)
+        dst = torch.as_tensor(np.asarray(offsets, dtype=np.int64)[g0:g1], device=device)[gid - g0] + e
+        out[dst] = w.to(dtype)
+        g0 = g1
+    return out

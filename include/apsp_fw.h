@@ -151,6 +151,21 @@ int apsp_fw_backward_f32(const float *d_grad_dist, const int32_t *d_path, const 
                          float *d_grad_w, int64_t n, int64_t ld, int64_t batch, int64_t stride,
                          int32_t *d_status, void *stream);
 
+
+/* ------------------------------------------------------------------------
+ * Phase timing (a measurement hook; the paper times whole runs only, §4.1).
+ * apsp_profile_enable(1) clears earlier records and starts bracketing every
+ * launch of apsp_fw_f32/apsp_fw_f64 with two CUDA events on the launch
+ * stream; apsp_profile_enable(0) stops recording (records are kept).
+ * apsp_profile_collect waits for the recorded events and returns, per phase
+ * index (0 = path init, 1 = phase 1 diagonal block, 2 = phases 2+3 panels,
+ * 3 = phase 4 min-plus), the summed device time in ms and the launch count.
+ * ms and launches must point to 4 entries each.  Not for use while a CUDA
+ * graph is being captured.
+ * ---------------------------------------------------------------------- */
+int apsp_profile_enable(int on);
+int apsp_profile_collect(double *ms, int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,8 @@ SIGNATURES = {
     "apsp_batched_set_variant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "apsp_batched_get_variant": (ctypes.c_int, [ctypes.c_int]),
     "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
+    "apsp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "apsp_profile_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
 }
 
 _lock = threading.Lock()
@@ -136,6 +138,22 @@ def apsp_fw(dist, path=None, stream=None):
     if dist.dtype == torch.float64:
         return apsp_fw_f64(dist, path, stream)
     raise TypeError(f"unsupported dtype {dist.dtype}")
+
+
+PHASES = ("path_init", "phase1_diag", "phase2_panels", "phase3_minplus")
+
+
+def profile_enable(on: bool = True):
+    """Start (clearing old records) or stop per-phase CUDA-event timing in the library."""
+    _check(load().apsp_profile_enable(1 if on else 0), "apsp_profile_enable")
+
+
+def profile_collect() -> dict:
+    """{phase: (total_ms, launches)} of the launches recorded since profile_enable(True)."""
+    ms = (ctypes.c_double * 4)()
+    cnt = (ctypes.c_int64 * 4)()
+    _check(load().apsp_profile_collect(ms, cnt), "apsp_profile_collect")
+    return {PHASES[p]: (float(ms[p]), int(cnt[p])) for p in range(4)}
 
 
 from .batched import BatchedPlan, apsp_fw_batched_f32, apsp_fw_batched  # noqa: E402

@@ -297,6 +297,56 @@ __global__ void __launch_bounds__(k3f64::THREADS)
 }
 
 // --------------------------------------------------------------------------
+// Phase timing hook: when enabled, each phase launch is bracketed by two CUDA
+// events recorded on the launch stream; apsp_profile_collect sums them.
+// --------------------------------------------------------------------------
+}  // namespace apsp
+#include <mutex>
+#include <vector>
+namespace apsp {
+struct PhaseRec {
+  int phase;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<PhaseRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+static cudaEvent_t prof_event() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII bracket around one launch (no-op when profiling is off).
+struct PhaseScope {
+  bool on;
+  PhaseRec rec;
+  cudaStream_t s;
+  PhaseScope(int phase, cudaStream_t st) : on(false), s(st) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    if (!g_prof_on) return;
+    on = true;
+    rec.phase = phase;
+    rec.a = prof_event();
+    rec.b = prof_event();
+    cudaEventRecord(rec.a, s);
+  }
+  ~PhaseScope() {
+    if (!on) return;
+    cudaEventRecord(rec.b, s);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_recs.push_back(rec);
+  }
+};
+
+// --------------------------------------------------------------------------
 // Host side: argument checks and the round loop (all launches on `stream`).
 // --------------------------------------------------------------------------
 constexpr int kMaxN = 65536;
@@ -344,13 +394,21 @@ static int run_fw(Real *D, int64_t n64, int64_t ld, int32_t *P, void *stream) {
   if (P) {
     const int64_t total = n64 * n64;
     const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+    PhaseScope ps(0, s);
     fw_path_init<<<blocks, 256, 0, s>>>(P, n64, ld);
   }
   const int R = (n + T - 1) / T;
   for (int r = 0; r < R; ++r) {
-    launch_phase1(D, ld, P, n, r, s);
+    {
+      PhaseScope ps(1, s);
+      launch_phase1(D, ld, P, n, r, s);
+    }
     if (R > 1) {
-      k2<<<2 * (R - 1), T2, smem2, s>>>(D, ld, P, n, r, R);
+      {
+        PhaseScope ps(2, s);
+        k2<<<2 * (R - 1), T2, smem2, s>>>(D, ld, P, n, r, R);
+      }
+      PhaseScope ps(3, s);
       launch_phase3(D, ld, P, n, r, R, s);
     }
   }
@@ -384,3 +442,31 @@ APSP_EXPORT const char *apsp_status_string(int status) {
 }
 
 APSP_EXPORT int apsp_version(void) { return 100; }
+
+APSP_EXPORT int apsp_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(apsp::g_prof_mu);
+  for (auto &r : apsp::g_prof_recs) {
+    apsp::g_prof_pool.push_back(r.a);
+    apsp::g_prof_pool.push_back(r.b);
+  }
+  apsp::g_prof_recs.clear();
+  apsp::g_prof_on = on != 0;
+  return APSP_OK;
+}
+
+APSP_EXPORT int apsp_profile_collect(double *ms, int64_t *launches) {
+  if (!ms || !launches) return APSP_EINVAL;
+  for (int p = 0; p < 4; ++p) {
+    ms[p] = 0.0;
+    launches[p] = 0;
+  }
+  std::lock_guard<std::mutex> g(apsp::g_prof_mu);
+  for (auto &r : apsp::g_prof_recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return APSP_ECUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return APSP_ECUDA;
+    ms[r.phase] += t;
+    launches[r.phase] += 1;
+  }
+  return APSP_OK;
+}

@@ -312,3 +312,13 @@ def test_generator_shape_of_workload():
     assert (np.diag(W) == 0).all()
     sizes = graphgen.batch_sizes(4096, 16, 512, 1)
     assert sizes.min() >= 16 and sizes.max() <= 512 and abs(sizes.mean() - 264) < 10
+
+
+def test_batched_generator_numpy_equals_torch():
+    pytest.importorskip("torch")
+    sizes = [3, 17, 1, 40]
+    off = np.array([0, 12, 304, 308], dtype=np.int64)
+    total = 308 + 1600
+    packed = graphgen.batched_graphs_torch(sizes, 0.3, 9, off, total).numpy()
+    for g, m in enumerate(graphgen.batched_graphs(sizes, 0.3, 9)):
+        np.testing.assert_array_equal(packed[off[g]:off[g] + m.size], m.reshape(-1))
