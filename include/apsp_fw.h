@@ -164,6 +164,12 @@ int apsp_fw_backward_f32(const float *d_grad_dist, const int32_t *d_path, const 
  * graph is being captured.
  * ---------------------------------------------------------------------- */
 int apsp_profile_enable(int on);
+
+/* Synchronizes `stream`, then returns and clears the error word that the
+ * single-graph kernels set on the device when one of their bounded waits for
+ * an asynchronous copy runs out (the kernel then leaves its block unchanged):
+ * APSP_OK if no wait ran out since the last call, else APSP_ECUDA. */
+int apsp_device_status(void *stream);
 int apsp_profile_collect(double *ms, int64_t *launches);
 
 #ifdef __cplusplus

@@ -40,6 +40,7 @@ SIGNATURES = {
     "apsp_batched_get_variant": (ctypes.c_int, [ctypes.c_int]),
     "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
     "apsp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "apsp_device_status": (ctypes.c_int, [_p]),
     "apsp_profile_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
 }
 
@@ -138,6 +139,11 @@ def apsp_fw(dist, path=None, stream=None):
     if dist.dtype == torch.float64:
         return apsp_fw_f64(dist, path, stream)
     raise TypeError(f"unsupported dtype {dist.dtype}")
+
+
+def device_status(stream=None) -> int:
+    """Synchronize the stream; return (and clear) the kernels' device-side error word."""
+    return int(load().apsp_device_status(_stream_ptr(stream)))
 
 
 PHASES = ("path_init", "phase1_diag", "phase2_panels", "phase3_minplus")

@@ -1,0 +1,104 @@
+"""Autotuner for the batched kernel: per size class, time every kernel variant
+(block edge / register tile) on synthetic graphs of that class and keep the
+fastest.
+
+The batched launch solves graphs of several size classes at once; each class
+may use a different variant (variant 0: 128 x 128 blocks with 8 x 8 register
+tiles; variant 1: 64 x 64 blocks with 4 x 4 tiles).  Choices are cached per
+device name in a JSON file and applied with :func:`apply_cached`.
+
+Timing only: every variant computes the same distances (bit-exact on integer
+weights), so the choice never changes results on integer inputs.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import batched as _b
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def _class_sizes(cls: int, count: int, seed: int):
+    lo, hi = _b.class_bounds(cls)
+    hi = min(hi, 512)
+    rng = np.random.default_rng(seed + cls)
+    return rng.integers(lo, hi + 1, size=count).astype(np.int64)
+
+
+def _time_plan(torch, sizes, W, D, P, reps: int) -> float:
+    plan = _b.BatchedPlan(sizes, _b.packed_offsets(sizes))
+    D.copy_(W)
+    plan.run(D, P)  # warm-up
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        D.copy_(W)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        plan.run(D, P)
+        e.record()
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    plan.close()
+    return float(np.median(times))
+
+
+def autotune(device="cuda:0", graphs_per_class: int = 608, reps: int = 3, seed: int = 7,
+             save: bool = True, verbose: bool = False) -> dict:
+    """Choose a variant per size class; returns {class: {"variant", "ms": [per variant]}}."""
+    import torch
+
+    import graphgen
+
+    result = {}
+    for cls in range(_b.num_classes()):
+        sizes = _class_sizes(cls, graphs_per_class, seed)
+        off = _b.packed_offsets(sizes)
+        total = _b.packed_numel(sizes)
+        W = graphgen.batched_graphs_torch(sizes, 0.3, seed, off, total, device=device)
+        D = torch.empty_like(W)
+        P = torch.empty(total, dtype=torch.int32, device=device)
+        ms = []
+        for v in range(_b.num_variants(cls)):
+            _b.set_variant(cls, v)
+            ms.append(_time_plan(torch, sizes, W, D, P, reps))
+        best = int(np.argmin(ms))
+        _b.set_variant(cls, best)
+        result[cls] = {"variant": best, "ms": ms, "bounds": list(_b.class_bounds(cls))}
+        if verbose:
+            print(f"class {cls} {_b.class_bounds(cls)}: variant ms {ms} -> {best}")
+        del W, D, P
+    if save:
+        name = torch.cuda.get_device_name(torch.device(device))
+        cache = {}
+        if os.path.exists(CACHE):
+            try:
+                cache = json.load(open(CACHE))
+            except Exception:
+                cache = {}
+        cache[name] = {str(c): r["variant"] for c, r in result.items()}
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return result
+
+
+def apply_cached(device="cuda:0") -> bool:
+    """Apply cached choices for this device, if any.  Returns whether any were applied."""
+    import torch
+    if not os.path.exists(CACHE):
+        return False
+    try:
+        cache = json.load(open(CACHE))
+    except Exception:
+        return False
+    choice = cache.get(torch.cuda.get_device_name(torch.device(device)))
+    if not choice:
+        return False
+    for c, v in choice.items():
+        _b.set_variant(int(c), int(v))
+    return True

@@ -34,60 +34,71 @@ namespace apsp {
 
 constexpr int kBatchedMaxN = 1024;
 
-// Size classes and their kernel variants (selected by the autotuner).  The
-// variant changes how a class's graphs are processed inside the one launch.
-//   variant 0: blocked, TB = 128 (all phases on 8 x 8 register tiles)
+// Size classes and their kernel variants (chosen by the autotuner, see
+// apsp_batched_set_variant).  A variant fixes the block edge and register
+// tile used for the class's graphs inside the one launch:
+//   variant 0: TB = 128, 8 x 8 outputs per thread
+//   variant 1: TB = 64,  4 x 4 outputs per thread (less padding for small n)
 constexpr int kNumClasses = 4;
 static const int32_t kClassLo[kNumClasses] = {1, 65, 129, 257};
 static const int32_t kClassHi[kNumClasses] = {64, 128, 256, kBatchedMaxN};
-constexpr int kNumVariants = 1;
-static int g_variant[kNumClasses] = {0, 0, 0, 0};
+__host__ __device__ constexpr int class_of_n(int32_t n) {
+  return n <= 64 ? 0 : n <= 128 ? 1 : n <= 256 ? 2 : 3;
+}
+constexpr int kNumVariants = 2;
+static int g_variant[kNumClasses] = {1, 0, 0, 0};
+
+static int class_of(int32_t n) { return class_of_n(n); }
 
 union BatchedSmem {
-  mp32::Smem prod;
-  mp32::DiagSmem diag;
+  mp32::SmemT<128> prod128;
+  mp32::SmemT<64> prod64;
+  mp32::DiagSmemT<128> diag128;
+  mp32::DiagSmemT<64> diag64;
 };
 
+template <int TM>
 __device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *__restrict__ P,
-                                                int n, BatchedSmem &sm) {
-  using mp32::T;
+                                                int n, BatchedSmem &smu) {
+  constexpr int T = 16 * TM;
+  auto &prod = *reinterpret_cast<mp32::SmemT<T> *>(&smu);
+  auto &diag = *reinterpret_cast<mp32::DiagSmemT<T> *>(&smu);
   const int ld = n;
   const int vec_ok = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
-  if (P) {
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[e] = -1;
-  }
-  __syncthreads();
   const int R = (n + T - 1) / T;
   for (int r = 0; r < R; ++r) {
     const int base = r * T, m = min(T, n - base);
-    mp32::diag_closure(D, ld, P, base, m, sm.diag);
+    __syncthreads();
+    mp32::diag_closure<TM>(D, ld, P, base, m, diag);
     __syncthreads();
     for (int J = 0; J < R; ++J) {
       if (J == r) continue;
-      mp32::block_product(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, vec_ok, sm.prod);
+      mp32::block_product<TM>(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, vec_ok, prod);
     }
     for (int I = 0; I < R; ++I) {
       if (I == r) continue;
-      mp32::block_product(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, vec_ok, sm.prod);
+      mp32::block_product<TM>(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, vec_ok, prod);
     }
     __syncthreads();
     for (int I = 0; I < R; ++I) {
       if (I == r) continue;
       for (int J = 0; J < R; ++J) {
         if (J == r) continue;
-        mp32::block_product(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m,
-                            vec_ok, sm.prod);
+        mp32::block_product<TM>(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m,
+                                vec_ok, prod);
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
+// Work item t: graph order[t] & 0x3fffffff, variant order[t] >> 30.
 __global__ void __launch_bounds__(mp32::THREADS, 2)
     fw_batched_persistent_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
                               const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
                               const int64_t *__restrict__ offs, int num, int *__restrict__ counter) {
-  __shared__ __align__(16) BatchedSmem sm;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  BatchedSmem &sm = *reinterpret_cast<BatchedSmem *>(smem_raw);
   __shared__ int s_next;
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
@@ -95,9 +106,19 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
     const int t = s_next;
     __syncthreads();  // all threads have read s_next before it is overwritten
     if (t >= num) break;
-    const int g = order[t];
+    const int item = order[t];
+    const int g = item & 0x3fffffff, variant = (int)((unsigned)item >> 30);
     const int64_t off = offs[g];
-    solve_graph_f32(Dp + off, Pp ? Pp + off : nullptr, ns[g], sm);
+    const int n = ns[g];
+    float *D = Dp + off;
+    int32_t *P = Pp ? Pp + off : nullptr;
+    if (P) {
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[e] = -1;
+    }
+    if (variant == 1)
+      solve_graph_f32<4>(D, P, n, sm);
+    else
+      solve_graph_f32<8>(D, P, n, sm);
   }
 }
 
@@ -116,6 +137,7 @@ namespace {
 
 int validate(const int32_t *h_n, const int64_t *h_off, int32_t num) {
   if (num < 0 || (num > 0 && (!h_n || !h_off))) return APSP_EINVAL;
+  if (num > (1 << 30)) return APSP_EUNSUPPORTED;
   for (int32_t g = 0; g < num; ++g) {
     if (h_n[g] < 1 || h_n[g] > apsp::kBatchedMaxN) return h_n[g] < 1 ? APSP_EINVAL : APSP_EUNSUPPORTED;
     if (h_off[g] < 0 || (h_off[g] & 3)) return APSP_EINVAL;
@@ -123,19 +145,27 @@ int validate(const int32_t *h_n, const int64_t *h_off, int32_t num) {
   return APSP_OK;
 }
 
+// Largest graphs first (longest processing time first); each entry carries
+// the variant of its size class in bits 30-31.
 std::vector<int32_t> lpt_order(const int32_t *h_n, int32_t num) {
   std::vector<int32_t> order(num);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return h_n[a] > h_n[b]; });
+  for (auto &g : order) g |= apsp::g_variant[apsp::class_of(h_n[g])] << 30;
   return order;
 }
+
+int g_smem_batched[64];
 
 int grid_for(int32_t num) {
   int dev = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  if (apsp::ensure_smem(apsp::fw_batched_persistent_f32, (int)sizeof(apsp::BatchedSmem), g_smem_batched))
+    return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apsp::fw_batched_persistent_f32,
-                                                    apsp::mp32::THREADS, 0) != cudaSuccess)
+                                                    apsp::mp32::THREADS,
+                                                    sizeof(apsp::BatchedSmem)) != cudaSuccess)
     return -1;
   const int g = sms * std::max(occ, 1);
   return std::max(1, std::min<int>(g, num));
@@ -194,7 +224,7 @@ APSP_EXPORT int apsp_fw_batched_run_f32(const apsp_batched_plan *p, float *d_dis
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaGetLastError();
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) return APSP_ECUDA;
-  apsp::fw_batched_persistent_f32<<<p->grid, apsp::mp32::THREADS, 0, s>>>(
+  apsp::fw_batched_persistent_f32<<<p->grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
       d_dist, d_path, p->d_order, p->d_n, p->d_off, p->num, p->d_counter);
   return apsp::status_from(cudaGetLastError());
 }
@@ -223,8 +253,8 @@ APSP_EXPORT int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice, s);
   int grid = grid_for(num);
   if (e == cudaSuccess && grid > 0) {
-    apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, 0, s>>>(d_dist, d_path, d_order, d_n,
-                                                                          d_off, num, d_counter);
+    apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
+        d_dist, d_path, d_order, d_n, d_off, num, d_counter);
     e = cudaGetLastError();
   }
   // Copies from pageable host memory have consumed their sources when they
@@ -257,3 +287,4 @@ APSP_EXPORT int apsp_batched_set_variant(int cls, int variant) {
 APSP_EXPORT int apsp_batched_get_variant(int cls) {
   return (cls < 0 || cls >= apsp::kNumClasses) ? -1 : apsp::g_variant[cls];
 }
+

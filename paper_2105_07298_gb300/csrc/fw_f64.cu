@@ -1,0 +1,585 @@
+// FP64 blocked Floyd-Warshall for sm_103a, exact, on the FP32 pipes.
+//
+// GB300 executes FP64 adds and mins at about 2 per clock per SM, 1/64 of its
+// FP32 rate, so a native FP64 min-plus product runs ~60x slower than FP32.
+// This path keeps every result bit-exact with IEEE FP64 (round to nearest)
+// while doing almost all of the work in FP32:
+//
+//  * each FP64 operand x is held as the float interval [rd(x), ru(x)]
+//    (largest float <= x, smallest float >= x);
+//  * a candidate a + b then lies in [lo, up] with lo = rd(rd(a) + rd(b)) and
+//    up = ru(ru(a) + ru(b)) (packed add.rm.f32x2 / add.rp.f32x2), and so does
+//    its FP64 rounding fl(a + b), since rounding is monotone;
+//  * the min-plus product keeps min lo and min up per output.  If
+//    min lo >= ru(old) nothing can beat the old value; if min lo == min up
+//    the exact FP64 minimum IS that float (integer-valued weights always land
+//    here); otherwise the few candidates with lo <= min(min up, ru(old)) are
+//    evaluated with a real FP64 add, warp-cooperatively.
+//
+// Schedule per round r (TB = 128), the blocked FW of §2.2:
+//  K1  fw64_diag         phase 1: Algorithm 1 on block (r,r), k sequential,
+//                        with the same interval filter per relaxation; also
+//                        packs the closed block as a product operand.
+//  K2a fw64_pack_panels  packs row blocks (r,J) and column blocks (I,r).
+//  K2b fw64_product<1,2> phases 2 and 3 as min-plus products with the closed
+//                        diagonal block: (r,J) <- min(C, D*(r,r) (x) C) and
+//                        (I,r) <- min(C, C (x) D*(r,r)) (the sequential k loop
+//                        over a panel block equals one product with the
+//                        closure); re-packs the updated blocks.
+//  K3  fw64_product<0>   phase 4: (I,J) <- min(C, D(I,r) (x) D(r,J)).
+// On integer-valued weights all sums are exact and D equals every correct FW;
+// on real weights phases 2/3 round through the closure instead of a chain of
+// sums, within the same error bound (relative ~ path length x 2^-53).
+#include <float.h>
+#include <stdint.h>
+
+#include "bulk.cuh"
+#include "common.cuh"
+#include "profile.h"
+
+namespace apsp {
+namespace f64 {
+
+constexpr int T = 128;
+constexpr int THREADS = 512;  // product: 16 warps, 4 x 8 outputs per thread
+constexpr int KS = 32, KP = 16, STAGES = 2;
+constexpr uint32_t SLAB_BYTES = KP * T * 8;
+
+// One operand block packed for the product kernel.  For an A operand
+// (A[i][k]): lo[kp][i] = (rd A[i][2kp], rd A[i][2kp+1]), hi likewise with ru,
+// rlo[i][k] = rd A[i][k], rhi[i][k] = ru A[i][k], r64[i][k] = A[i][k].
+// For a B operand (B[k][j]): lo[kp][j] = (rd B[2kp][j], rd B[2kp+1][j]), ...,
+// rlo[j][k] = rd B[k][j], rhi[j][k], r64[j][k] = B[k][j] (transposed).
+// Entries outside the matrix hold +inf.
+struct Pack {
+  unsigned long long lo[T / 2][T];
+  unsigned long long hi[T / 2][T];
+  float rlo[T][T];
+  float rhi[T][T];
+  double r64[T][T];
+};
+
+// ---------------------------------------------------------------- bounds
+// Largest float <= x and smallest float >= x for any non-NaN double, from the
+// bit pattern (integer pipes only).  Tight in the normal float range; below
+// it the bound is loosened to 0 / +-FLT_MIN, which keeps it valid.
+__device__ __forceinline__ float f64_up(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if ((b << 1) == 0) return 0.0f;
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ff);
+  if (e == 0x7ff) return sign ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000);
+  const int fe = e - 1023 + 127;
+  if (fe >= 255) return sign ? -FLT_MAX : __int_as_float(0x7f800000);
+  if (fe <= 0) return sign ? -0.0f : FLT_MIN;
+  const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned f = sign | ((unsigned)fe << 23) | m23;  // toward zero
+  if ((lo & 0x1fffffffu) && !sign) f += 1u;
+  return __uint_as_float(f);
+}
+
+__device__ __forceinline__ float f64_down(double x) { return -f64_up(-x); }
+
+// Exact float -> double bits (integer pipes; subnormal floats via cvt).
+__device__ __forceinline__ unsigned long long f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xff;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0) {
+    if ((u & 0x7fffffu) == 0) return sign;
+    return (unsigned long long)__double_as_longlong((double)f);
+  }
+  if (e == 0xff) return sign | 0x7ff0000000000000ull | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return sign | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+}
+
+// Signed integer key with the order of the doubles (-0 sorts just below +0;
+// neither arises from sums of the non-negative-cycle inputs except -0 + -0).
+__device__ __forceinline__ long long dkey(unsigned long long b) {
+  return (long long)(b ^ ((unsigned long long)((long long)b >> 63) >> 1));
+}
+__device__ __forceinline__ unsigned long long dkey_bits(long long k) {
+  return (unsigned long long)k ^ ((unsigned long long)(k >> 63) >> 1);
+}
+
+__device__ __forceinline__ unsigned long long packf2(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+
+__device__ __forceinline__ void relax2_rm(float &acc, unsigned long long a, unsigned long long b) {
+  asm("{\n\t.reg .b64 t;\n\t.reg .f32 x, y;\n\t"
+      "add.rm.f32x2 t, %1, %2;\n\t"
+      "mov.b64 {x, y}, t;\n\t"
+      "min.f32 %0, %0, x, y;\n\t}"
+      : "+f"(acc)
+      : "l"(a), "l"(b));
+}
+__device__ __forceinline__ void relax2_rp(float &acc, unsigned long long a, unsigned long long b) {
+  asm("{\n\t.reg .b64 t;\n\t.reg .f32 x, y;\n\t"
+      "add.rp.f32x2 t, %1, %2;\n\t"
+      "mov.b64 {x, y}, t;\n\t"
+      "min.f32 %0, %0, x, y;\n\t}"
+      : "+f"(acc)
+      : "l"(a), "l"(b));
+}
+
+// ---------------------------------------------------------------- packing
+// Packs a T x T block held in shared memory (row stride S, +inf padded) as
+// an A operand (as_b = false) or a B operand (as_b = true).
+template <int S>
+__device__ void pack_block(const double *s, Pack *pk, bool as_b) {
+  for (int e = threadIdx.x; e < T * T / 2; e += blockDim.x) {
+    const int kp = e / T, x = e % T;
+    const double v0 = as_b ? s[(2 * kp) * S + x] : s[x * S + 2 * kp];
+    const double v1 = as_b ? s[(2 * kp + 1) * S + x] : s[x * S + 2 * kp + 1];
+    pk->lo[kp][x] = packf2(f64_down(v0), f64_down(v1));
+    pk->hi[kp][x] = packf2(f64_up(v0), f64_up(v1));
+  }
+  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+    const int x = e / T, k = e % T;  // row x of the row-contiguous copies
+    const double v = as_b ? s[k * S + x] : s[x * S + k];
+    pk->rlo[x][k] = f64_down(v);
+    pk->rhi[x][k] = f64_up(v);
+    pk->r64[x][k] = v;
+  }
+}
+
+// ---------------------------------------------------------------- K1
+// Phase 1 on block (r,r): Algorithm 1 (strict "<", k ascending).  Each
+// element keeps an upper float bound dhi beside it, and the lower bounds of
+// the pivot row and column are published per step, so a relaxation whose
+// lower bound rd(rd(d_ik) + rd(d_kj)) is not below dhi_ij is skipped without
+// an FP64 add (it cannot be an improvement).  The owners of row/column k+1
+// publish their lower bounds after their step-k update (one barrier per
+// step).  Then the closed block is packed as the A operand of the row-panel
+// products and the B operand of the column-panel products.
+constexpr int K1_THREADS = 1024;
+struct K1Smem {
+  double d[T * T];
+  float dhi[T * T];
+  float rlo[2][T];  // rd of row k of the block
+  float clo[2][T];  // rd of column k of the block
+};
+
+__global__ void __launch_bounds__(K1_THREADS)
+    fw64_diag(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
+              Pack *diagA, Pack *diagB) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  K1Smem &sm = *reinterpret_cast<K1Smem *>(smem_raw);
+  constexpr int EPT = T * T / K1_THREADS;
+  const int base = r * T, m = min(T, n - base), tid = threadIdx.x;
+  const double INF = inf<double>();
+  for (int e = tid; e < T * T; e += K1_THREADS) {
+    const int i = e / T, j = e % T;
+    const double v = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : INF;
+    sm.d[e] = v;
+    sm.dhi[e] = f64_up(v);
+    if (i == 0) sm.rlo[0][j] = f64_down(v);
+    if (j == 0) sm.clo[0][i] = f64_down(v);
+  }
+  int pk[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) pk[q] = -1;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    const int buf = k & 1, nb = buf ^ 1;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = tid + q * K1_THREADS;
+      const int i = e / T, j = e % T;
+      const float lo = __fadd_rd(sm.clo[buf][i], sm.rlo[buf][j]);
+      if (lo < sm.dhi[e]) {
+        const double cand = __dadd_rn(sm.d[i * T + k], sm.d[k * T + j]);
+        if (cand < sm.d[e]) {
+          sm.d[e] = cand;
+          sm.dhi[e] = f64_up(cand);
+          pk[q] = base + k;
+        }
+      }
+      if (i == k + 1) sm.rlo[nb][j] = f64_down(sm.d[e]);
+      if (j == k + 1) sm.clo[nb][i] = f64_down(sm.d[e]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const int e = tid + q * K1_THREADS;
+    const int i = e / T, j = e % T;
+    if (i < m && j < m && pk[q] >= 0) {
+      const int64_t g = (int64_t)(base + i) * ld + base + j;
+      D[g] = sm.d[e];
+      if (P) P[g] = pk[q];
+    }
+  }
+  if (diagA) {
+    pack_block<T>(sm.d, diagA, false);
+    pack_block<T>(sm.d, diagB, true);
+  }
+}
+
+// ---------------------------------------------------------------- K2a
+// Packs the round's row blocks (r,J) as B operands (packB[J]) and column
+// blocks (I,r) as A operands (packA[I]), before phases 2/3 update them.
+constexpr int K2A_THREADS = 512;
+__global__ void __launch_bounds__(K2A_THREADS)
+    fw64_pack_panels(const double *__restrict__ D, int64_t ld, int n, int r, int R, Pack *packA,
+                     Pack *packB) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double *s = reinterpret_cast<double *>(smem_raw);
+  constexpr int S = T + 1;
+  const int b = blockIdx.x;
+  const bool is_row = b < R - 1;
+  int other = is_row ? b : b - (R - 1);
+  other += (other >= r);
+  const int base_r = r * T, m_r = min(T, n - base_r);
+  const int base_o = other * T, m_o = min(T, n - base_o);
+  const int rows = is_row ? m_r : m_o, cols = is_row ? m_o : m_r;
+  const int64_t row0 = is_row ? base_r : base_o, col0 = is_row ? base_o : base_r;
+  for (int e = threadIdx.x; e < T * T; e += K2A_THREADS) {
+    const int i = e / T, j = e % T;
+    s[i * S + j] = (i < rows && j < cols) ? D[(row0 + i) * ld + col0 + j] : inf<double>();
+  }
+  __syncthreads();
+  pack_block<S>(s, is_row ? &packB[other] : &packA[other], is_row);
+}
+
+// ---------------------------------------------------------------- products
+// MODE 0: phase 4, C = (I,J), A = packA[I], B = packB[J] (grid (R-1)^2)
+// MODE 1: phase 2, C = (r,J), A = diagA,    B = packB[J] (grid R-1), re-packs C into packB[J]
+// MODE 2: phase 3, C = (I,r), A = packA[I], B = diagB    (grid R-1), re-packs C into packA[I]
+struct ProdSmem {
+  unsigned long long Alo[STAGES][KP][T];
+  unsigned long long Ahi[STAGES][KP][T];
+  unsigned long long Blo[STAGES][KP][T];
+  unsigned long long Bhi[STAGES][KP][T];
+  uint64_t bar[STAGES];
+};
+
+// Thread (warp w, lane l): wy = w/2 (0..7), wx = w%2, ly = l/8, lx = l%8;
+//   rows i(r) = (r>>1)*64 + wy*8 + ly*2 + (r&1)            (r = 0..3)
+//   cols j(c) = (c>>2)*64 + wx*32 + ((c>>1)&1)*16 + lx*2 + (c&1)   (c = 0..7)
+__device__ __forceinline__ int row4(int r, int wy, int ly) {
+  return (r >> 1) * 64 + wy * 8 + ly * 2 + (r & 1);
+}
+__device__ __forceinline__ int col8(int c, int wx, int lx) {
+  return (c >> 2) * 64 + wx * 32 + ((c >> 1) & 1) * 16 + lx * 2 + (c & 1);
+}
+
+__device__ __forceinline__ void issue_slab(ProdSmem &sm, int st, const Pack *A, const Pack *B, int s) {
+  mbar_expect_tx(&sm.bar[st], 4 * SLAB_BYTES);
+  bulk_g2s(&sm.Alo[st][0][0], &A->lo[s * KP][0], SLAB_BYTES, &sm.bar[st]);
+  bulk_g2s(&sm.Ahi[st][0][0], &A->hi[s * KP][0], SLAB_BYTES, &sm.bar[st]);
+  bulk_g2s(&sm.Blo[st][0][0], &B->lo[s * KP][0], SLAB_BYTES, &sm.bar[st]);
+  bulk_g2s(&sm.Bhi[st][0][0], &B->hi[s * KP][0], SLAB_BYTES, &sm.bar[st]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    fw64_product(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R,
+                 Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  ProdSmem &sm = *reinterpret_cast<ProdSmem *>(smem_raw);
+  int I, J;
+  if (MODE == 0) {
+    I = blockIdx.x / (R - 1);
+    J = blockIdx.x % (R - 1);
+    I += (I >= r);
+    J += (J >= r);
+  } else if (MODE == 1) {
+    I = r;
+    J = blockIdx.x + (blockIdx.x >= r);
+  } else {
+    I = blockIdx.x + (blockIdx.x >= r);
+    J = r;
+  }
+  const Pack *A = MODE == 1 ? diagA : &packA[I];
+  const Pack *B = MODE == 2 ? diagB : &packB[J];
+  const int baseI = I * T, baseJ = J * T, baseK = r * T;
+  const int mI = min(T, n - baseI), mJ = min(T, n - baseJ), mK = min(T, n - baseK);
+  const int nslab = (mK + KS - 1) / KS;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int wy = w >> 1, wx = w & 1, ly = lane >> 3, lx = lane & 7;
+  const float FINF = __int_as_float(0x7f800000);
+
+  if (tid == 0) {
+    for (int st = 0; st < STAGES; ++st) mbar_init(&sm.bar[st], 1);
+    fence_mbar_init();
+    for (int s = 0; s < STAGES && s < nslab; ++s) issue_slab(sm, s, A, B, s);
+  }
+  __syncthreads();
+
+  float lo[4][8], up[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) lo[a][c] = up[a][c] = FINF;
+
+  for (int s = 0; s < nslab; ++s) {
+    const int st = s % STAGES;
+    const bool ok = mbar_wait(&sm.bar[st], (s / STAGES) & 1);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(&g_device_error, APSP_ECUDA);
+        for (int s2 = s + 1; s2 < nslab && s2 < s + STAGES; ++s2)
+          mbar_wait(&sm.bar[s2 % STAGES], (s2 / STAGES) & 1);
+      }
+      return;
+    }
+#pragma unroll 1
+    for (int kp = 0; kp < KP; ++kp) {
+      unsigned long long a[4], b[8];
+#pragma unroll
+      for (int rr = 0; rr < 4; rr += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Alo[st][kp][row4(rr, wy, ly)]);
+        a[rr] = t.x;
+        a[rr + 1] = t.y;
+      }
+#pragma unroll
+      for (int cc = 0; cc < 8; cc += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Blo[st][kp][col8(cc, wx, lx)]);
+        b[cc] = t.x;
+        b[cc + 1] = t.y;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) relax2_rm(lo[rr][cc], a[rr], b[cc]);
+#pragma unroll
+      for (int rr = 0; rr < 4; rr += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Ahi[st][kp][row4(rr, wy, ly)]);
+        a[rr] = t.x;
+        a[rr + 1] = t.y;
+      }
+#pragma unroll
+      for (int cc = 0; cc < 8; cc += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bhi[st][kp][col8(cc, wx, lx)]);
+        b[cc] = t.x;
+        b[cc + 1] = t.y;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) relax2_rp(up[rr][cc], a[rr], b[cc]);
+    }
+    __syncthreads();
+    if (tid == 0 && s + STAGES < nslab) {
+      fence_proxy_async_smem();
+      issue_slab(sm, st, A, B, s + STAGES);
+    }
+  }
+
+  // Epilogue.  The ring is free: min-lo and min-up go to shared memory, then
+  // each warp owns 8 whole rows (lane l: columns 4l..4l+3) in compact rolled
+  // loops (small code, coalesced global accesses).  Per output:
+  //   X = min lo >= ru(old):          nothing can beat old;
+  //   X == min up (exact min = X):    improved iff X < old; P recovered below;
+  //   otherwise ("slow"):             exact FP64 resolution below.
+  // D may be written at once: the recovery reads only the packed operands.
+  float *Lo = reinterpret_cast<float *>(smem_raw);  // [T][T]
+  float *Up = Lo + T * T;                           // [T][T]
+  __syncthreads();
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < 8; cc += 2) {
+      const int i = row4(rr, wy, ly), j = col8(cc, wx, lx);
+      *reinterpret_cast<float2 *>(&Lo[i * T + j]) = make_float2(lo[rr][cc], lo[rr][cc + 1]);
+      *reinterpret_cast<float2 *>(&Up[i * T + j]) = make_float2(up[rr][cc], up[rr][cc + 1]);
+    }
+  __syncthreads();
+  const int j0 = 4 * lane;
+#pragma unroll 1
+  for (int i = w * 8; i < w * 8 + 8; ++i) {
+    if (i >= mI) break;
+    double *row = D + (int64_t)(baseI + i) * ld + baseJ;
+    unsigned quick = 0u, slow = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + q;
+      if (j >= mJ) continue;
+      const double old = row[j];
+      const float X = Lo[i * T + j];
+      if (!(X < f64_up(old))) continue;
+      if (X == Up[i * T + j]) {
+        const unsigned long long xb = f32_to_f64_bits(X);
+        if (dkey(xb) < dkey((unsigned long long)__double_as_longlong(old))) {
+          row[j] = __longlong_as_double((long long)xb);
+          quick |= 1u << q;
+        }
+      } else {
+        slow |= 1u << q;
+      }
+    }
+    unsigned todo = quick | slow;
+    unsigned bal = __ballot_sync(kFullMask, todo != 0);
+    if (!bal) continue;
+    const float4 alo = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
+    const float4 ahi = reinterpret_cast<const float4 *>(&A->rhi[i][0])[lane];
+    const float la[4] = {alo.x, alo.y, alo.z, alo.w}, ha[4] = {ahi.x, ahi.y, ahi.z, ahi.w};
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      const unsigned stodo = __shfl_sync(kFullMask, todo, src);
+      const unsigned sslow = __shfl_sync(kFullMask, slow, src);
+      const int q0 = __ffs(stodo) - 1;
+      if (lane == src) todo &= todo - 1;
+      if (!(stodo & (stodo - 1))) bal &= bal - 1;
+      const bool is_slow = (sslow >> q0) & 1u;
+      const int sj = 4 * src + q0;
+      const int64_t g = (int64_t)(baseI + i) * ld + baseJ + sj;
+      const float X = Lo[i * T + sj];
+      const double old = D[g];  // quick: already the new value (unused)
+      const float th = is_slow ? fminf(Up[i * T + sj], f64_up(old)) : X;
+      const float4 blo = reinterpret_cast<const float4 *>(&B->rlo[sj][0])[lane];
+      const float4 bhi = reinterpret_cast<const float4 *>(&B->rhi[sj][0])[lane];
+      const float lb[4] = {blo.x, blo.y, blo.z, blo.w}, hb[4] = {bhi.x, bhi.y, bhi.z, bhi.w};
+      long long best = 0x7fffffffffffffffll;
+      int bestk = 0x7fffffff;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * lane + q;
+        const float l = __fadd_rd(la[q], lb[q]);
+        if (l <= th) {
+          const float u = __fadd_ru(ha[q], hb[q]);
+          unsigned long long vb;
+          if (l == u) vb = f32_to_f64_bits(l);
+          else vb = (unsigned long long)__double_as_longlong(__dadd_rn(A->r64[i][k], B->r64[sj][k]));
+          const long long key = dkey(vb);
+          if (key < best) {
+            best = key;
+            bestk = k;
+          }
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {  // warp argmin over (key, k)
+        const long long ob = __shfl_xor_sync(kFullMask, best, off);
+        const int okk = __shfl_xor_sync(kFullMask, bestk, off);
+        if (ob < best || (ob == best && okk < bestk)) {
+          best = ob;
+          bestk = okk;
+        }
+      }
+      if (lane == 0 && bestk != 0x7fffffff) {
+        if (is_slow) {
+          if (best < dkey((unsigned long long)__double_as_longlong(old))) {
+            D[g] = __longlong_as_double((long long)dkey_bits(best));
+            if (P) P[g] = baseK + bestk;
+          }
+        } else if (P) {
+          P[g] = baseK + bestk;
+        }
+      }
+    }
+  }
+  if (MODE == 0) return;
+  // Phases 2/3: re-pack the updated block for this round's phase 4.
+  __syncthreads();
+  Pack *dst = MODE == 1 ? &packB[J] : &packA[I];
+#pragma unroll
+  for (int rr = 0; rr < 4; rr += 2) {
+    const int i0 = row4(rr, wy, ly);  // rows i0, i0 + 1
+#pragma unroll
+    for (int cc = 0; cc < 8; cc += 2) {
+      const int j0 = col8(cc, wx, lx);  // cols j0, j0 + 1
+      double v[2][2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          v[a][c] = (i0 + a < mI && j0 + c < mJ) ? D[(int64_t)(baseI + i0 + a) * ld + baseJ + j0 + c]
+                                                 : inf<double>();
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int i = i0 + a, j = j0 + c;
+          const float vl = f64_down(v[a][c]), vh = f64_up(v[a][c]);
+          if (MODE == 1) {  // B operand: [j][k = i]
+            dst->rlo[j][i] = vl;
+            dst->rhi[j][i] = vh;
+            dst->r64[j][i] = v[a][c];
+          } else {  // A operand: [i][k = j]
+            dst->rlo[i][j] = vl;
+            dst->rhi[i][j] = vh;
+            dst->r64[i][j] = v[a][c];
+          }
+        }
+      if (MODE == 1) {  // pairs along k = rows i0, i0 + 1
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          dst->lo[i0 / 2][j0 + c] = packf2(f64_down(v[0][c]), f64_down(v[1][c]));
+          dst->hi[i0 / 2][j0 + c] = packf2(f64_up(v[0][c]), f64_up(v[1][c]));
+        }
+      } else {  // pairs along k = cols j0, j0 + 1
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          dst->lo[j0 / 2][i0 + a] = packf2(f64_down(v[a][0]), f64_down(v[a][1]));
+          dst->hi[j0 / 2][i0 + a] = packf2(f64_up(v[a][0]), f64_up(v[a][1]));
+        }
+      }
+    }
+  }
+}
+
+static int g_smem_k1[64], g_smem_k2a[64], g_smem_p0[64], g_smem_p1[64], g_smem_p2[64];
+
+}  // namespace f64
+
+// Host round loop for FP64 (called by apsp_fw_f64).
+int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s) {
+  using namespace f64;
+  const int R = (n + T - 1) / T;
+  int st;
+  const int smem1 = (int)sizeof(K1Smem), smem2a = T * (T + 1) * 8, smemp = (int)sizeof(ProdSmem);
+  if ((st = ensure_smem(fw64_diag, smem1, g_smem_k1))) return st;
+  if ((st = ensure_smem(fw64_pack_panels, smem2a, g_smem_k2a))) return st;
+  if ((st = ensure_smem(fw64_product<0>, smemp, g_smem_p0))) return st;
+  if ((st = ensure_smem(fw64_product<1>, smemp, g_smem_p1))) return st;
+  if ((st = ensure_smem(fw64_product<2>, smemp, g_smem_p2))) return st;
+  char *scratch = nullptr;
+  Pack *packA = nullptr, *packB = nullptr, *diagA = nullptr, *diagB = nullptr;
+  if (R > 1) {
+    if (cudaMallocAsync((void **)&scratch, sizeof(Pack) * (2 * (size_t)R + 2), s) != cudaSuccess) {
+      cudaGetLastError();
+      return APSP_ENOMEM;
+    }
+    packA = reinterpret_cast<Pack *>(scratch);
+    packB = packA + R;
+    diagA = packB + R;
+    diagB = diagA + 1;
+  }
+  for (int r = 0; r < R; ++r) {
+    {
+      PhaseScope ps(1, s);
+      fw64_diag<<<1, K1_THREADS, smem1, s>>>(D, ld, P, n, r, diagA, diagB);
+    }
+    if (R > 1) {
+      {
+        PhaseScope ps(2, s);
+        fw64_pack_panels<<<2 * (R - 1), K2A_THREADS, smem2a, s>>>(D, ld, n, r, R, packA, packB);
+        fw64_product<1><<<R - 1, THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
+        fw64_product<2><<<R - 1, THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
+      }
+      PhaseScope ps(3, s);
+      fw64_product<0><<<(R - 1) * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA,
+                                                                 diagB);
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (scratch) {
+    cudaError_t f = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = f;
+  }
+  return status_from(e);
+}
+
+int take_device_error_f64() {
+  int v = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
+  if (v != 0 && cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
+  return v;
+}
+
+}  // namespace apsp

@@ -26,7 +26,9 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "bulk.cuh"
 #include "minplus_f32.cuh"
+#include "profile.h"
 
 namespace apsp {
 
@@ -43,66 +45,32 @@ __global__ void fw_path_init(int32_t *__restrict__ P, int64_t n, int64_t ld) {
 }
 
 // --------------------------------------------------------------------------
-// K1: phase 1 on the diagonal block (r,r).  One CTA; the block lives in shared
-// memory; T sequential steps separated by barriers.  Step k reads row k and
-// column k of the block, which step k itself never changes (D[k][k] = 0).
-// --------------------------------------------------------------------------
-template <typename Real, int T, int THREADS>
-__global__ void __launch_bounds__(THREADS) fw_phase1_diag(Real *__restrict__ D, int64_t ld,
-                                                          int32_t *__restrict__ P, int n, int r) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real *s = reinterpret_cast<Real *>(smem_raw);
-  constexpr int EPT = T * T / THREADS;
-  const int base = r * T;
-  const int m = min(T, n - base);
-  const int tid = threadIdx.x;
-  for (int e = tid; e < T * T; e += THREADS) {
-    const int i = e / T, j = e % T;
-    s[e] = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : inf<Real>();
-  }
-  int pk[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) pk[q] = -1;
-  __syncthreads();
-  for (int k = 0; k < m; ++k) {
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * THREADS;
-      const int i = e / T, j = e % T;
-      const Real cand = add_rn(s[i * T + k], s[k * T + j]);
-      if (cand < s[e]) {
-        s[e] = cand;
-        pk[q] = base + k;
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * THREADS;
-    const int i = e / T, j = e % T;
-    if (i < m && j < m && pk[q] >= 0) {
-      const int64_t g = (int64_t)(base + i) * ld + base + j;
-      D[g] = s[e];
-      if (P) P[g] = pk[q];
-    }
-  }
-}
-
-// --------------------------------------------------------------------------
 // K2: phases 2 and 3.  CTA b < R-1 owns row block (r, J), the others column
 // block (I, r).  The diagonal block (final after K1) and the own block sit in
-// shared memory; k runs sequentially over the round's vertices.
+// shared memory (row stride T+1: row and column walks are both free of bank
+// conflicts); k runs sequentially over the round's vertices.
 //   row block:    own[i][j] = min(own[i][j], diag[i][k] + own[k][j])
 //   column block: own[i][j] = min(own[i][j], own[i][k] + diag[k][j])
+// When `pan` is given (FP32), the finished blocks are also written, padded
+// with +inf to full T x T, in the layouts phase 4 reads this round:
+//   row block (r,J):    Bpan[J][kp][j] = (own[2kp][j], own[2kp+1][j]),
+//                       Bt[J][j][k] = own[k][j]
+//   column block (I,r): Apan[I][kp][i] = (own[i][2kp], own[i][2kp+1]),
+//                       Acp[I][i][k] = own[i][k]
 // --------------------------------------------------------------------------
+struct Panels {
+  unsigned long long *Apan, *Bpan;
+  float *Acp, *Bt;
+};
+
 template <typename Real, int T, int THREADS>
 __global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D, int64_t ld,
                                                             int32_t *__restrict__ P, int n, int r,
-                                                            int R) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+                                                            int R, Panels pan) {
+  constexpr int S = T + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Real *diag = reinterpret_cast<Real *>(smem_raw);
-  Real *own = diag + T * T;
+  Real *own = diag + T * S;
   constexpr int EPT = T * T / THREADS;
   const int b = blockIdx.x;
   const bool is_row = b < R - 1;
@@ -116,8 +84,8 @@ __global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D
   const int tid = threadIdx.x;
   for (int e = tid; e < T * T; e += THREADS) {
     const int i = e / T, j = e % T;
-    diag[e] = (i < m_r && j < m_r) ? D[(int64_t)(base_r + i) * ld + base_r + j] : inf<Real>();
-    own[e] = (i < rows && j < cols) ? D[(row0 + i) * ld + col0 + j] : inf<Real>();
+    diag[i * S + j] = (i < m_r && j < m_r) ? D[(int64_t)(base_r + i) * ld + base_r + j] : inf<Real>();
+    own[i * S + j] = (i < rows && j < cols) ? D[(row0 + i) * ld + col0 + j] : inf<Real>();
   }
   int pk[EPT];
 #pragma unroll
@@ -129,9 +97,9 @@ __global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D
       for (int q = 0; q < EPT; ++q) {
         const int e = tid + q * THREADS;
         const int i = e / T, j = e % T;
-        const Real cand = add_rn(diag[i * T + k], own[k * T + j]);
-        if (cand < own[e]) {
-          own[e] = cand;
+        const Real cand = add_rn(diag[i * S + k], own[k * S + j]);
+        if (cand < own[i * S + j]) {
+          own[i * S + j] = cand;
           pk[q] = base_r + k;
         }
       }
@@ -143,9 +111,9 @@ __global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D
       for (int q = 0; q < EPT; ++q) {
         const int e = tid + q * THREADS;
         const int i = e / T, j = e % T;
-        const Real cand = add_rn(own[i * T + k], diag[k * T + j]);
-        if (cand < own[e]) {
-          own[e] = cand;
+        const Real cand = add_rn(own[i * S + k], diag[k * S + j]);
+        if (cand < own[i * S + j]) {
+          own[i * S + j] = cand;
           pk[q] = base_r + k;
         }
       }
@@ -158,33 +126,26 @@ __global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D
     const int i = e / T, j = e % T;
     if (i < rows && j < cols && pk[q] >= 0) {
       const int64_t g = (row0 + i) * ld + col0 + j;
-      D[g] = own[e];
+      D[g] = own[i * S + j];
       if (P) P[g] = pk[q];
     }
   }
-}
-
-// --------------------------------------------------------------------------
-// Lazy argmin recovery (shared by the K3 variants).  All 32 lanes of a warp
-// call it with the same (gi, gj, target): target is min over the round's k of
-// fl(D[gi][baseK+k] + D[baseK+k][gj]).  Lanes test 32 consecutive k at a time;
-// the lowest k whose sum equals target (bit for bit, same rounding) is the k
-// the sequential loop would have recorded.
-// --------------------------------------------------------------------------
-template <typename Real>
-__device__ __forceinline__ void recover_argmin(const Real *__restrict__ D, int64_t ld,
-                                               int32_t *__restrict__ P, int64_t gi, int64_t gj,
-                                               Real target, int baseK, int mK, int lane) {
-  const Real *arow = D + gi * ld + baseK;
-  const Real *bcol = D + (int64_t)baseK * ld + gj;
-  for (int k0 = 0; k0 < mK; k0 += 32) {
-    const int k = k0 + lane;
-    bool hit = false;
-    if (k < mK) hit = (add_rn(arow[k], bcol[(int64_t)k * ld]) == target);
-    const unsigned bal = __ballot_sync(kFullMask, hit);
-    if (bal) {
-      if (lane == 0) P[gi * ld + gj] = baseK + k0 + (__ffs(bal) - 1);
-      return;
+  if constexpr (sizeof(Real) == 4) {
+    if (pan.Apan) {
+      const float *o = reinterpret_cast<const float *>(own);
+      const int64_t blk = other;
+      for (int e = tid; e < T * T / 2; e += THREADS) {
+        const int kp = e / T, x = e % T;  // x = j (row block) or i (column block)
+        const float lo = is_row ? o[(2 * kp) * S + x] : o[x * S + 2 * kp];
+        const float hi = is_row ? o[(2 * kp + 1) * S + x] : o[x * S + 2 * kp + 1];
+        const unsigned long long v =
+            ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+        (is_row ? pan.Bpan : pan.Apan)[(blk * (T / 2) + kp) * T + x] = v;
+      }
+      for (int e = tid; e < T * T; e += THREADS) {
+        const int x = e / T, k = e % T;  // Bt[J][j][k] = own[k][j]; Acp[I][i][k] = own[i][k]
+        (is_row ? pan.Bt : pan.Acp)[(blk * T + x) * T + k] = is_row ? o[k * S + x] : o[x * S + k];
+      }
     }
   }
 }
@@ -199,234 +160,282 @@ __global__ void __launch_bounds__(mp32::THREADS)
     fw_phase1_diag_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r) {
   __shared__ mp32::DiagSmem sm;
   const int base = r * mp32::T;
-  mp32::diag_closure(D, ld, P, base, min(mp32::T, n - base), sm);
+  mp32::diag_closure<8>(D, ld, P, base, min(mp32::T, n - base), sm);
 }
+
+// K3 (FP32) stages its operands with bulk copies from the panel buffers K2
+// wrote (already in the paired shared-memory layout and padded with +inf, so
+// the main loop needs no bounds checks): per 32-k slab one 16 KiB copy of A
+// and one of B into a two-stage ring, completion tracked by an mbarrier per
+// stage.  P recovery reads the row-contiguous copies Acp/Bt (one float4 of
+// each per lane: the 128 candidate sums of an output in one round trip).
+namespace k3 {
+constexpr int T = mp32::T, KS = mp32::KS, KP = mp32::KP, STAGES = 2;
+constexpr uint32_t SLAB_BYTES = KP * T * 8;  // one operand, one slab
+struct Smem {
+  unsigned long long As[STAGES][KP][T];
+  unsigned long long Bs[STAGES][KP][T];
+  uint64_t bar[STAGES];
+  int fail;
+};
+}  // namespace k3
 
 __global__ void __launch_bounds__(mp32::THREADS, 2)
     fw_phase3_minplus_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
-                          int R, int vec_ok) {
-  using mp32::T;
-  __shared__ __align__(16) mp32::Smem sm;
-  const int Rm = R - 1;
-  int I = blockIdx.x / Rm, J = blockIdx.x % Rm;
-  I += (I >= r);
-  J += (J >= r);
-  const int baseI = I * T, baseJ = J * T, baseK = r * T;
-  mp32::block_product(D, ld, P, baseI, baseJ, baseK, min(T, n - baseI), min(T, n - baseJ),
-                      min(T, n - baseK), vec_ok, sm);
-}
-
-// --------------------------------------------------------------------------
-// K3 (FP64): phase 4 with native FP64 add and min.  TB = 64, 256 threads,
-// 4 x 4 outputs per thread (rows ty + 16 r, cols tx + 16 c), k slabs of 16
-// staged k-major in shared memory.  Same epilogue and P recovery as FP32.
-// --------------------------------------------------------------------------
-namespace k3f64 {
-constexpr int T = 64;
-constexpr int THREADS = 256;
-constexpr int KS = 16;
-}  // namespace k3f64
-
-__global__ void __launch_bounds__(k3f64::THREADS)
-    fw_phase3_minplus_f64(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
-                          int R) {
-  using namespace k3f64;
-  __shared__ double As[KS][T + 1];
-  __shared__ double Bs[KS][T];
+                          int R, int vec_ok, Panels pan) {
+  using namespace k3;
+  using mp32::col_at;
+  using mp32::row_at;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   const int Rm = R - 1;
   int I = blockIdx.x / Rm, J = blockIdx.x % Rm;
   I += (I >= r);
   J += (J >= r);
   const int baseI = I * T, baseJ = J * T, baseK = r * T;
   const int mI = min(T, n - baseI), mJ = min(T, n - baseJ), mK = min(T, n - baseK);
-  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 4, tx = tid & 15;
-  const double INF = inf<double>();
-  double acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[a][c] = INF;
+  const int nslab = (mK + KS - 1) / KS;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ty = mp32::thread_ty(), tx = mp32::thread_tx();
+  const float INF = inf<float>();
+  const unsigned long long *srcA = pan.Apan + (int64_t)I * (T / 2) * T;
+  const unsigned long long *srcB = pan.Bpan + (int64_t)J * (T / 2) * T;
 
-  for (int k0 = 0; k0 < mK; k0 += KS) {
-    __syncthreads();
-    for (int e = tid; e < T * KS; e += THREADS) {
-      const int i = e / KS, k = e % KS;  // A[i][k0+k] -> As[k][i]
-      As[k][i] = (i < mI && k0 + k < mK) ? D[(int64_t)(baseI + i) * ld + baseK + k0 + k] : INF;
-      const int kb = e / T, j = e % T;  // B[k0+kb][j] -> Bs[kb][j]
-      Bs[kb][j] = (j < mJ && k0 + kb < mK) ? D[(int64_t)(baseK + k0 + kb) * ld + baseJ + j] : INF;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int k = 0; k < KS; ++k) {
-      double a[4], b[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[k][ty + 16 * q];
-        b[q] = Bs[k][tx + 16 * q];
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fmin(acc[x][y], __dadd_rn(a[x], b[y]));
+  if (tid == 0) {
+    sm.fail = 0;
+    for (int st = 0; st < STAGES; ++st) mbar_init(&sm.bar[st], 1);
+    fence_mbar_init();
+    for (int s = 0; s < STAGES && s < nslab; ++s) {
+      mbar_expect_tx(&sm.bar[s], 2 * SLAB_BYTES);
+      bulk_g2s(&sm.As[s][0][0], srcA + (int64_t)s * KP * T, SLAB_BYTES, &sm.bar[s]);
+      bulk_g2s(&sm.Bs[s][0][0], srcB + (int64_t)s * KP * T, SLAB_BYTES, &sm.bar[s]);
     }
   }
+  __syncthreads();
+
+  float acc[8][8];
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
-    const int i = ty + 16 * x;
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int j = tx + 16 * y;
-      bool imp = false;
-      if (i < mI && j < mJ) {
-        double *dst = D + (int64_t)(baseI + i) * ld + baseJ + j;
-        imp = acc[x][y] < *dst;
-        if (imp) *dst = acc[x][y];
+    for (int c = 0; c < 8; ++c) acc[a][c] = INF;
+
+  for (int s = 0; s < nslab; ++s) {
+    const int st = s % STAGES;
+    const bool ok = mbar_wait(&sm.bar[st], (s / STAGES) & 1);
+    if (__syncthreads_or(!ok)) {
+      // A copy never completed: record it, wait (bounded) for the other
+      // copies this CTA issued, and leave without touching D or P.
+      if (tid == 0) {
+        atomicExch(&g_device_error, APSP_ECUDA);
+        for (int s2 = s + 1; s2 < nslab && s2 < s + STAGES; ++s2)
+          mbar_wait(&sm.bar[s2 % STAGES], (s2 / STAGES) & 1);
       }
-      if (P) {
-        unsigned bal = __ballot_sync(kFullMask, imp);
-        while (bal) {
-          const int src = __ffs(bal) - 1;
-          bal &= bal - 1;
-          const double tgt = __shfl_sync(kFullMask, acc[x][y], src);
-          const int si = __shfl_sync(kFullMask, i, src), sj = __shfl_sync(kFullMask, j, src);
-          recover_argmin<double>(D, ld, P, baseI + si, baseJ + sj, tgt, baseK, mK, lane);
-        }
+      return;
+    }
+#pragma unroll 1  // no cross-iteration prefetch: keeps the kernel at <= 128 registers, no spills
+    for (int kp = 0; kp < KP; ++kp) {
+      unsigned long long a[8], b[8];
+#pragma unroll
+      for (int rr = 0; rr < 8; rr += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[st][kp][row_at(rr, ty)]);
+        a[rr] = t.x;
+        a[rr + 1] = t.y;
       }
+#pragma unroll
+      for (int cc = 0; cc < 8; cc += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[st][kp][col_at(cc, tx)]);
+        b[cc] = t.x;
+        b[cc + 1] = t.y;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) mp32::relax2(acc[rr][cc], a[rr], b[cc]);
+    }
+    __syncthreads();  // stage st fully read
+    if (tid == 0 && s + STAGES < nslab) {
+      fence_proxy_async_smem();
+      const int s2 = s + STAGES;
+      mbar_expect_tx(&sm.bar[st], 2 * SLAB_BYTES);
+      bulk_g2s(&sm.As[st][0][0], srcA + (int64_t)s2 * KP * T, SLAB_BYTES, &sm.bar[st]);
+      bulk_g2s(&sm.Bs[st][0][0], srcB + (int64_t)s2 * KP * T, SLAB_BYTES, &sm.bar[st]);
+    }
+  }
+
+  // Epilogue.  The ring is free now: the block of new candidates goes to
+  // shared memory so that the rest runs as compact rolled loops with each
+  // warp owning 16 whole rows (lane l: columns 4l..4l+3), which keeps the
+  // code small (instruction-cache friendly) and every global access coalesced.
+  float *Cs = reinterpret_cast<float *>(smem_raw);  // [T][T]
+  __syncthreads();
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < 8; cc += 2)
+      *reinterpret_cast<float2 *>(&Cs[row_at(rr, ty) * T + col_at(cc, tx)]) =
+          make_float2(acc[rr][cc], acc[rr][cc + 1]);
+  __syncthreads();
+  const float *acp = pan.Acp + (int64_t)I * T * T;
+  const float *bt = pan.Bt + (int64_t)J * T * T;
+  const int w = tid >> 5, j0 = 4 * lane;
+#pragma unroll 1
+  for (int i = w * 16; i < w * 16 + 16; ++i) {
+    if (i >= mI) break;
+    const float4 c = *reinterpret_cast<const float4 *>(&Cs[i * T + j0]);
+    float *row = D + (int64_t)(baseI + i) * ld + baseJ;
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+    float ov[4] = {INF, INF, INF, INF};
+    if (vec_ok && j0 + 3 < mJ) {
+      const float4 o = *reinterpret_cast<const float4 *>(row + j0);
+      ov[0] = o.x; ov[1] = o.y; ov[2] = o.z; ov[3] = o.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (j0 + q < mJ) ov[q] = row[j0 + q];
+    }
+    unsigned imp = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (j0 + q < mJ && cv[q] < ov[q]) imp |= 1u << q;
+    if (imp) {
+      if (vec_ok && j0 + 3 < mJ) {
+        *reinterpret_cast<float4 *>(row + j0) =
+            make_float4(imp & 1 ? cv[0] : ov[0], imp & 2 ? cv[1] : ov[1], imp & 4 ? cv[2] : ov[2],
+                        imp & 8 ? cv[3] : ov[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (imp >> q & 1) row[j0 + q] = cv[q];
+      }
+    }
+    if (!P) continue;
+    // P: one improved output per warp pass; lane l tests k = 4l..4l+3.
+    unsigned bal = __ballot_sync(kFullMask, imp != 0);
+    if (!bal) continue;
+    const float4 av = reinterpret_cast<const float4 *>(acp + i * T)[lane];
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      const unsigned sim = __shfl_sync(kFullMask, imp, src);
+      const int q = __ffs(sim) - 1;
+      if (lane == src) imp &= imp - 1;
+      if (!(sim & (sim - 1))) bal &= bal - 1;  // src has no further improved output
+      const int sj = 4 * src + q;
+      const float tgt = Cs[i * T + sj];
+      const float4 bv = reinterpret_cast<const float4 *>(bt + sj * T)[lane];
+      const unsigned h = (__fadd_rn(av.x, bv.x) == tgt ? 1u : 0u) | (__fadd_rn(av.y, bv.y) == tgt ? 2u : 0u) |
+                         (__fadd_rn(av.z, bv.z) == tgt ? 4u : 0u) | (__fadd_rn(av.w, bv.w) == tgt ? 8u : 0u);
+      const unsigned hb = __ballot_sync(kFullMask, h != 0);
+      const int L = __ffs(hb) - 1;  // hb != 0: tgt is one of the candidates
+      const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
+      if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj] = baseK + 4 * L + (__ffs(hL) - 1);
     }
   }
 }
 
-// --------------------------------------------------------------------------
-// Phase timing hook: when enabled, each phase launch is bracketed by two CUDA
-// events recorded on the launch stream; apsp_profile_collect sums them.
-// --------------------------------------------------------------------------
-}  // namespace apsp
-#include <mutex>
-#include <vector>
-namespace apsp {
-struct PhaseRec {
-  int phase;
-  cudaEvent_t a, b;
-};
-static std::mutex g_prof_mu;
-static bool g_prof_on = false;
-static std::vector<PhaseRec> g_prof_recs;
-static std::vector<cudaEvent_t> g_prof_pool;
-
-static cudaEvent_t prof_event() {
-  if (!g_prof_pool.empty()) {
-    cudaEvent_t e = g_prof_pool.back();
-    g_prof_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-// RAII bracket around one launch (no-op when profiling is off).
-struct PhaseScope {
-  bool on;
-  PhaseRec rec;
-  cudaStream_t s;
-  PhaseScope(int phase, cudaStream_t st) : on(false), s(st) {
-    std::lock_guard<std::mutex> g(g_prof_mu);
-    if (!g_prof_on) return;
-    on = true;
-    rec.phase = phase;
-    rec.a = prof_event();
-    rec.b = prof_event();
-    cudaEventRecord(rec.a, s);
-  }
-  ~PhaseScope() {
-    if (!on) return;
-    cudaEventRecord(rec.b, s);
-    std::lock_guard<std::mutex> g(g_prof_mu);
-    g_prof_recs.push_back(rec);
-  }
-};
+// Phase timing state (see profile.h).
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<PhaseRec> g_prof_recs;
+std::vector<cudaEvent_t> g_prof_pool;
 
 // --------------------------------------------------------------------------
 // Host side: argument checks and the round loop (all launches on `stream`).
 // --------------------------------------------------------------------------
 constexpr int kMaxN = 65536;
 
-template <typename Real> struct Cfg;
-template <> struct Cfg<float> {
-  static constexpr int T = mp32::T, T2 = 1024;
-};
-template <> struct Cfg<double> {
-  static constexpr int T = 64, T2 = 512;
-};
+constexpr int kT32 = mp32::T, kT64 = 128, kK2Threads = 1024;
+static int g_smem_p2f[64], g_smem_k3[64];
 
-static int g_smem_p2f[64], g_smem_p2d[64];
+int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s);
+int take_device_error_f64();
 
-static int launch_phase3(float *D, int64_t ld, int32_t *P, int n, int r, int R, cudaStream_t s) {
-  const int vec_ok = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
-  fw_phase3_minplus_f32<<<(R - 1) * (R - 1), mp32::THREADS, 0, s>>>(D, ld, P, n, r, R, vec_ok);
-  return APSP_OK;
+static void path_init(int32_t *P, int64_t n, int64_t ld, cudaStream_t s) {
+  const int64_t total = n * n;
+  const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
+  PhaseScope ps(0, s);
+  fw_path_init<<<blocks, 256, 0, s>>>(P, n, ld);
 }
-static void launch_phase1(float *D, int64_t ld, int32_t *P, int n, int r, cudaStream_t s) {
-  fw_phase1_diag_f32<<<1, mp32::THREADS, 0, s>>>(D, ld, P, n, r);
-}
-static void launch_phase1(double *D, int64_t ld, int32_t *P, int n, int r, cudaStream_t s) {
-  constexpr int T = 64, T1 = 512;
-  fw_phase1_diag<double, T, T1><<<1, T1, T * T * sizeof(double), s>>>(D, ld, P, n, r);
-}
-static int launch_phase3(double *D, int64_t ld, int32_t *P, int n, int r, int R, cudaStream_t s) {
-  fw_phase3_minplus_f64<<<(R - 1) * (R - 1), k3f64::THREADS, 0, s>>>(D, ld, P, n, r, R);
+
+static int check_args(const void *D, int64_t n, int64_t ld) {
+  if (n < 0 || n > kMaxN) return APSP_EINVAL;
+  if (n == 0) return APSP_OK;
+  if (!D || ld < n) return APSP_EINVAL;
   return APSP_OK;
 }
 
-template <typename Real>
-static int run_fw(Real *D, int64_t n64, int64_t ld, int32_t *P, void *stream) {
-  if (n64 < 0 || n64 > kMaxN) return APSP_EINVAL;
-  if (n64 == 0) return APSP_OK;
-  if (!D || ld < n64) return APSP_EINVAL;
+static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *stream) {
+  int st = check_args(D, n64, ld);
+  if (st || n64 == 0) return st;
   const int n = (int)n64;
-  constexpr int T = Cfg<Real>::T, T2 = Cfg<Real>::T2;
+  constexpr int T = kT32;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int smem2 = 2 * T * T * (int)sizeof(Real);
-  auto k2 = fw_phase2_panels<Real, T, T2>;
-  const int st = ensure_smem(k2, smem2, sizeof(Real) == 4 ? g_smem_p2f : g_smem_p2d);
-  if (st) return st;
+  const int smem2 = 2 * T * (T + 1) * (int)sizeof(float);
+  auto k2 = fw_phase2_panels<float, T, kK2Threads>;
+  if ((st = ensure_smem(k2, smem2, g_smem_p2f))) return st;
+  if ((st = ensure_smem(fw_phase3_minplus_f32, (int)sizeof(k3::Smem), g_smem_k3))) return st;
   cudaGetLastError();  // clear any stale error so the checks below are ours
-  if (P) {
-    const int64_t total = n64 * n64;
-    const int blocks = (int)((total + 255) / 256 < 152 * 32 ? (total + 255) / 256 : 152 * 32);
-    PhaseScope ps(0, s);
-    fw_path_init<<<blocks, 256, 0, s>>>(P, n64, ld);
-  }
   const int R = (n + T - 1) / T;
+  // Phase-4 operand panels, written by K2 each round (4 arrays of R*T*T
+  // 4-byte words); stream-ordered scratch, freed after the last round.
+  Panels pan{};
+  char *scratch = nullptr;
+  if (R > 1) {
+    const size_t words = (size_t)R * T * T;
+    if (cudaMallocAsync((void **)&scratch, 4 * words * 4, s) != cudaSuccess) {
+      cudaGetLastError();
+      return APSP_ENOMEM;
+    }
+    pan.Apan = reinterpret_cast<unsigned long long *>(scratch);
+    pan.Bpan = reinterpret_cast<unsigned long long *>(scratch + words * 4);
+    pan.Acp = reinterpret_cast<float *>(scratch + 2 * words * 4);
+    pan.Bt = reinterpret_cast<float *>(scratch + 3 * words * 4);
+  }
+  if (P) path_init(P, n64, ld, s);
+  const int vec_ok = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
   for (int r = 0; r < R; ++r) {
     {
       PhaseScope ps(1, s);
-      launch_phase1(D, ld, P, n, r, s);
+      fw_phase1_diag_f32<<<1, mp32::THREADS, 0, s>>>(D, ld, P, n, r);
     }
     if (R > 1) {
       {
         PhaseScope ps(2, s);
-        k2<<<2 * (R - 1), T2, smem2, s>>>(D, ld, P, n, r, R);
+        k2<<<2 * (R - 1), kK2Threads, smem2, s>>>(D, ld, P, n, r, R, pan);
       }
       PhaseScope ps(3, s);
-      launch_phase3(D, ld, P, n, r, R, s);
+      fw_phase3_minplus_f32<<<(R - 1) * (R - 1), mp32::THREADS, sizeof(k3::Smem), s>>>(D, ld, P, n, r,
+                                                                                      R, vec_ok, pan);
     }
   }
-  return status_from(cudaGetLastError());
+  cudaError_t e = cudaGetLastError();
+  if (scratch) {
+    cudaError_t f = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = f;
+  }
+  return status_from(e);
+}
+
+static int run_fw_f64(double *D, int64_t n64, int64_t ld, int32_t *P, void *stream) {
+  int st = check_args(D, n64, ld);
+  if (st || n64 == 0) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  if (P) path_init(P, n64, ld, s);
+  return run_fw_f64_interval(D, (int)n64, ld, P, s);
 }
 
 }  // namespace apsp
 
 APSP_EXPORT int apsp_fw_f32(float *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream) {
-  return apsp::run_fw<float>(d_dist, n, ld, d_path, stream);
+  return apsp::run_fw_f32(d_dist, n, ld, d_path, stream);
 }
 
 APSP_EXPORT int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream) {
-  return apsp::run_fw<double>(d_dist, n, ld, d_path, stream);
+  return apsp::run_fw_f64(d_dist, n, ld, d_path, stream);
 }
 
 APSP_EXPORT int apsp_fw_block_size(int elem_bytes) {
-  return elem_bytes == 4 ? apsp::Cfg<float>::T : elem_bytes == 8 ? apsp::Cfg<double>::T : 0;
+  return elem_bytes == 4 ? apsp::kT32 : elem_bytes == 8 ? apsp::kT64 : 0;
 }
 
 APSP_EXPORT const char *apsp_status_string(int status) {
@@ -469,4 +478,15 @@ APSP_EXPORT int apsp_profile_collect(double *ms, int64_t *launches) {
     launches[r.phase] += 1;
   }
   return APSP_OK;
+}
+
+APSP_EXPORT int apsp_device_status(void *stream) {
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return APSP_ECUDA;
+  int v = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbol(&v, apsp::g_device_error, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
+  if (v != 0 && cudaMemcpyToSymbol(apsp::g_device_error, &zero, sizeof(int)) != cudaSuccess)
+    return APSP_ECUDA;
+  const int v64 = apsp::take_device_error_f64();
+  return v != 0 ? v : v64;
 }

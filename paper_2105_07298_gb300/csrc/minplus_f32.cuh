@@ -2,7 +2,8 @@
 // building blocks of the FP32 kernels (single-graph phase 4 and the batched
 // kernel).  Internal header.
 //
-// Block product (one CTA of 256 threads, TB = 128):
+// Block product (one CTA of 256 threads, TB = 16 * TM, TM x TM outputs per
+// thread; TM = 8 gives TB = 128, TM = 4 gives TB = 64):
 //     C[i][j] <- min(C[i][j], min_k A[i][k] + B[k][j]),  P[i][j] <- argmin k
 // for a TB x TB block C of the matrix D, A = block (I,K), B = block (K,J).
 // This is phase 4 of the blocked FW of §2.2 and, with A or B the closed
@@ -25,30 +26,32 @@
 namespace apsp {
 namespace mp32 {
 
-constexpr int T = 128;        // block edge
-constexpr int THREADS = 256;  // 8 warps, 8 x 8 outputs per thread
+constexpr int THREADS = 256;  // 8 warps
 constexpr int KS = 32;        // k per shared-memory slab
 constexpr int KP = KS / 2;    // k-pairs per slab
+constexpr int T = 128;        // block edge of the TM = 8 configuration
 
 // Shared layout of one slab: As[kp][i] = (A[i][2kp], A[i][2kp+1]),
 // Bs[kp][j] = (B[2kp][j], B[2kp+1][j]), 8 bytes per pair.
-struct Smem {
-  unsigned long long As[KP][T];
-  unsigned long long Bs[KP][T];
+template <int TB>
+union SmemT {
+  struct {
+    unsigned long long As[KP][TB];
+    unsigned long long Bs[KP][TB];
+  };
+  float Cs[TB][TB];  // epilogue: the block of new candidates
 };
+using Smem = SmemT<T>;
 
-// Thread (warp w, lane l), wy = w/2, wx = w%2, ly = l/8, lx = l%8:
-//   rows i(r) = (r>>2)*64 + wy*16 + ((r>>1)&1)*8 + ly*2 + (r&1)
-//   cols j(c) = (c>>2)*64 + wx*32 + ((c>>1)&1)*16 + lx*2 + (c&1)
-// Consecutive r (c) pairs are adjacent rows (columns), so each pair is one
-// 16-byte shared load; one k-pair of a warp touches 64 (A) and 128 (B)
-// consecutive bytes, free of bank conflicts.
-__device__ __forceinline__ int row_of(int r, int wy, int ly) {
-  return (r >> 2) * 64 + wy * 16 + ((r >> 1) & 1) * 8 + ly * 2 + (r & 1);
-}
-__device__ __forceinline__ int col_of(int c, int wx, int lx) {
-  return (c >> 2) * 64 + wx * 32 + ((c >> 1) & 1) * 16 + lx * 2 + (c & 1);
-}
+// Thread (warp w, lane l): ty = (w/2)*4 + l/8 (0..15), tx = (w%2)*8 + l%8
+// (0..15); its TM rows and TM columns come in adjacent pairs:
+//   rows i(r) = (r>>1)*32 + ty*2 + (r&1),  cols j(c) = (c>>1)*32 + tx*2 + (c&1).
+// Each pair is one 16-byte shared load; one k-pair of a warp touches 64 (A)
+// and 128 (B) consecutive bytes, free of bank conflicts.
+__device__ __forceinline__ int thread_ty() { return ((threadIdx.x >> 5) >> 1) * 4 + ((threadIdx.x & 31) >> 3); }
+__device__ __forceinline__ int thread_tx() { return ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7); }
+__device__ __forceinline__ int row_at(int r, int ty) { return (r >> 1) * 32 + ty * 2 + (r & 1); }
+__device__ __forceinline__ int col_at(int c, int tx) { return (c >> 1) * 32 + tx * 2 + (c & 1); }
 
 __device__ __forceinline__ void relax2(float &acc, unsigned long long a, unsigned long long b) {
   asm("{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
@@ -64,44 +67,55 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
 }
 
 // Warp-cooperative first-argmin (all 32 lanes, warp-uniform arguments).
-// arow[k] = A[i][k], bcol[k * ld] = B[k][j] for k < mK.
+// arow[k] = A[i][k], bcol[k * ld] = B[k][j] for k < mK <= T.  All T/32 loads
+// of a lane are issued before the first compare, so an output costs one
+// memory round trip.
+template <int TB>
 __device__ __forceinline__ int first_argmin(const float *arow, const float *bcol, int64_t ld,
                                             float target, int mK, int lane) {
-  for (int k0 = 0; k0 < mK; k0 += 32) {
-    const int k = k0 + lane;
-    bool hit = false;
-    if (k < mK) hit = (__fadd_rn(arow[k], bcol[(int64_t)k * ld]) == target);
-    const unsigned bal = __ballot_sync(kFullMask, hit);
-    if (bal) return k0 + (__ffs(bal) - 1);
+  constexpr int Q = TB / 32;
+  float s[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int k = q * 32 + lane;
+    s[q] = (k < mK) ? __fadd_rn(arow[k], bcol[(int64_t)k * ld]) : inf<float>();
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int k = q * 32 + lane;
+    const unsigned bal = __ballot_sync(kFullMask, k < mK && s[q] == target);
+    if (bal) return q * 32 + (__ffs(bal) - 1);
   }
   return -1;  // unreachable when target is one of the candidates
 }
 
 // C(baseI, baseJ) <- min(C, A(baseI, baseK) (x) B(baseK, baseJ)).  mI, mJ, mK:
-// valid extents (<= T) of the row, column and k ranges.  vec_ok: ld % 4 == 0
+// valid extents (<= TB) of the row, column and k ranges.  vec_ok: ld % 4 == 0
 // and D 16-byte aligned (enables 16/8-byte global accesses).  The epilogue
 // first recovers P (reading A and B from global memory), then waits at a
 // barrier, then writes C, so C may be the same block as A or B (phases 2/3).
 // Must be called by all 256 threads of the CTA.
+template <int TM>
 __device__ __forceinline__ void block_product(float *__restrict__ D, int64_t ld,
                                               int32_t *__restrict__ P, int baseI, int baseJ,
                                               int baseK, int mI, int mJ, int mK, int vec_ok,
-                                              Smem &sm) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int wy = w >> 1, wx = w & 1, ly = lane >> 3, lx = lane & 7;
+                                              SmemT<16 * TM> &sm) {
+  constexpr int TB = 16 * TM;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ty = thread_ty(), tx = thread_tx();
   const float INF = inf<float>();
 
-  float acc[8][8];
+  float acc[TM][TM];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[a][c] = INF;
+    for (int c = 0; c < TM; ++c) acc[a][c] = INF;
 
   for (int k0 = 0; k0 < mK; k0 += KS) {
     __syncthreads();  // previous slab (or previous use of sm) fully consumed
-    // A slab: 128 rows x 32 k; a float4 along k gives two pairs
+    // A slab: TB rows x 32 k; a float4 along k gives two pairs
 #pragma unroll
-    for (int q = 0; q < (T * KS / 4) / THREADS; ++q) {
+    for (int q = 0; q < (TB * KS / 4) / THREADS; ++q) {
       const int idx = tid + q * THREADS;
       const int i = idx >> 3, k4 = (idx & 7) * 4;
       const int kk = k0 + k4;
@@ -117,11 +131,11 @@ __device__ __forceinline__ void block_product(float *__restrict__ D, int64_t ld,
       sm.As[k4 / 2][i] = pack2(v[0], v[1]);
       sm.As[k4 / 2 + 1][i] = pack2(v[2], v[3]);
     }
-    // B slab: rows k and k+1 over 128 columns -> pairs
+    // B slab: rows k and k+1 over TB columns -> pairs
 #pragma unroll
-    for (int q = 0; q < (KP * T / 4) / THREADS; ++q) {
+    for (int q = 0; q < (KP * TB / 4) / THREADS; ++q) {
       const int idx = tid + q * THREADS;
-      const int kp = idx >> 5, j4 = (idx & 31) * 4;
+      const int kp = idx / (TB / 4), j4 = (idx % (TB / 4)) * 4;
       const int kk = k0 + 2 * kp;
       float v0[4], v1[4];
       const float *s0 = D + (int64_t)(baseK + kk) * ld + baseJ + j4;
@@ -143,159 +157,162 @@ __device__ __forceinline__ void block_product(float *__restrict__ D, int64_t ld,
       dst[1] = make_ulonglong2(pack2(v0[2], v1[2]), pack2(v0[3], v1[3]));
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 1
     for (int kp = 0; kp < KP; ++kp) {
-      unsigned long long a[8], b[8];
+      unsigned long long a[TM], b[TM];
 #pragma unroll
-      for (int rr = 0; rr < 8; rr += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[kp][row_of(rr, wy, ly)]);
+      for (int rr = 0; rr < TM; rr += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[kp][row_at(rr, ty)]);
         a[rr] = t.x;
         a[rr + 1] = t.y;
       }
 #pragma unroll
-      for (int cc = 0; cc < 8; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[kp][col_of(cc, wx, lx)]);
+      for (int cc = 0; cc < TM; cc += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[kp][col_at(cc, tx)]);
         b[cc] = t.x;
         b[cc + 1] = t.y;
       }
 #pragma unroll
-      for (int rr = 0; rr < 8; ++rr)
+      for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) relax2(acc[rr][cc], a[rr], b[cc]);
+        for (int cc = 0; cc < TM; ++cc) relax2(acc[rr][cc], a[rr], b[cc]);
     }
   }
 
-  // Epilogue 1: improvement flags against the old block (one bit per output).
-  unsigned long long imp = 0ull;
+  // Epilogue.  The new candidates go to shared memory; then each warp owns
+  // TB/8 whole rows (lane l: columns CPL*l .. CPL*l+CPL-1), in compact rolled
+  // loops.  Pass 1 computes the improvement flags and recovers P, reading A
+  // and B from global memory; pass 2 (after a barrier) writes the improved
+  // outputs, so C may be the same block as A or B (phases 2/3).
+  constexpr int CPL = TB / 32, RPW = TB / 8;
+  __syncthreads();
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr) {
-    const int i = row_of(rr, wy, ly);
-    const float *src = D + (int64_t)(baseI + i) * ld + baseJ;
+  for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
-    for (int cc = 0; cc < 8; cc += 2) {
-      const int j = col_of(cc, wx, lx);
-      if (i < mI) {
-        float o0 = INF, o1 = INF;
-        if (vec_ok && j + 1 < mJ) {
-          const float2 o = *reinterpret_cast<const float2 *>(src + j);
-          o0 = o.x;
-          o1 = o.y;
-        } else {
-          if (j < mJ) o0 = src[j];
-          if (j + 1 < mJ) o1 = src[j + 1];
-        }
-        if (j < mJ && acc[rr][cc] < o0) imp |= 1ull << (rr * 8 + cc);
-        if (j + 1 < mJ && acc[rr][cc + 1] < o1) imp |= 1ull << (rr * 8 + cc + 1);
-      }
-    }
-  }
-  // Epilogue 2: P recovery for improved outputs, one output per warp pass.
-  if (P) {
+    for (int cc = 0; cc < TM; cc += 2)
+      *reinterpret_cast<float2 *>(&sm.Cs[row_at(rr, ty)][col_at(cc, tx)]) =
+          make_float2(acc[rr][cc], acc[rr][cc + 1]);
+  __syncthreads();
+  const int w = tid >> 5, j0 = CPL * lane;
+  unsigned long long flags = 0ull;  // bit (t * CPL + q): row w*RPW + t, column j0 + q
+#pragma unroll 1
+  for (int t = 0; t < RPW; ++t) {
+    const int i = w * RPW + t;
+    if (i >= mI) break;
+    const float *row = D + (int64_t)(baseI + i) * ld + baseJ;
+    unsigned imp = 0u;
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
+    for (int q = 0; q < CPL; ++q)
+      if (j0 + q < mJ && sm.Cs[i][j0 + q] < row[j0 + q]) imp |= 1u << q;
+    flags |= (unsigned long long)imp << (t * CPL);
+    if (!P) continue;
+    unsigned bal = __ballot_sync(kFullMask, imp != 0);
+    if (!bal) continue;
+    const float *arow = D + (int64_t)(baseI + i) * ld + baseK;
+    float av[CPL];
 #pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
-        unsigned bal = __ballot_sync(kFullMask, (imp >> (rr * 8 + cc)) & 1ull);
-        while (bal) {
-          const int src = __ffs(bal) - 1;
-          bal &= bal - 1;
-          const float tgt = __shfl_sync(kFullMask, acc[rr][cc], src);
-          const int si = row_of(rr, __shfl_sync(kFullMask, wy, src), __shfl_sync(kFullMask, ly, src));
-          const int sj = col_of(cc, __shfl_sync(kFullMask, wx, src), __shfl_sync(kFullMask, lx, src));
-          const int64_t gi = baseI + si, gj = baseJ + sj;
-          const int k = first_argmin(D + gi * ld + baseK, D + (int64_t)baseK * ld + gj, ld, tgt,
-                                     mK, lane);
-          if (lane == 0 && k >= 0) P[gi * ld + gj] = baseK + k;
-        }
-      }
+    for (int q = 0; q < CPL; ++q) av[q] = (j0 + q < mK) ? arow[j0 + q] : INF;
+    while (bal) {
+      const int src = __ffs(bal) - 1;
+      const unsigned sim = __shfl_sync(kFullMask, imp, src);
+      const int q0 = __ffs(sim) - 1;
+      if (lane == src) imp &= imp - 1;
+      if (!(sim & (sim - 1))) bal &= bal - 1;
+      const int sj = CPL * src + q0;
+      const float tgt = sm.Cs[i][sj];
+      const float *bcol = D + (int64_t)baseK * ld + baseJ + sj;
+      unsigned h = 0u;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+        if (j0 + q < mK && __fadd_rn(av[q], bcol[(int64_t)(j0 + q) * ld]) == tgt) h |= 1u << q;
+      const unsigned hb = __ballot_sync(kFullMask, h != 0);
+      const int L = __ffs(hb) - 1;
+      const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
+      if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj] = baseK + CPL * L + (__ffs(hL) - 1);
     }
   }
   __syncthreads();  // every read of A and B (staging and recovery) precedes the writes
-  // Epilogue 3: write the improved outputs.
+#pragma unroll 1
+  for (int t = 0; t < RPW; ++t) {
+    const unsigned imp = (unsigned)(flags >> (t * CPL)) & ((1u << CPL) - 1);
+    if (!imp) continue;
+    const int i = w * RPW + t;
+    float *row = D + (int64_t)(baseI + i) * ld + baseJ;
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr) {
-    const int i = row_of(rr, wy, ly);
-    float *dst = D + (int64_t)(baseI + i) * ld + baseJ;
-#pragma unroll
-    for (int cc = 0; cc < 8; cc += 2) {
-      const int j = col_of(cc, wx, lx);
-      const bool i0 = (imp >> (rr * 8 + cc)) & 1ull, i1 = (imp >> (rr * 8 + cc + 1)) & 1ull;
-      if (i0 && i1 && vec_ok) {
-        *reinterpret_cast<float2 *>(dst + j) = make_float2(acc[rr][cc], acc[rr][cc + 1]);
-      } else {
-        if (i0) dst[j] = acc[rr][cc];
-        if (i1) dst[j + 1] = acc[rr][cc + 1];
-      }
-    }
+    for (int q = 0; q < CPL; ++q)
+      if (imp >> q & 1) row[j0 + q] = sm.Cs[i][j0 + q];
   }
 }
 
 // Register-resident classic FW (Algorithm 1, strict "<") on the diagonal
-// block (base, base): every thread keeps its 8 x 8 outputs in registers; at
-// step k the owners of row k and column k publish them to shared memory (two
-// alternating buffers, one barrier per step).  Step k never changes row or
-// column k (D[k][k] = 0), so the published values are the ones every thread
-// must use.  Writes D (all valid outputs) and P (where improved).
-struct DiagSmem {
-  float row[2][T];
-  float col[2][T];
+// block (base, base) of edge TB = 16 * TM: every thread keeps its TM x TM
+// outputs in registers; at step k the owners of row k and column k publish
+// them to shared memory (two alternating buffers, one barrier per step).
+// Step k never changes row or column k (D[k][k] = 0), so the published values
+// are the ones every thread must use.  Writes D (all valid outputs) and P
+// (where improved).
+template <int TB>
+struct DiagSmemT {
+  float row[2][TB];
+  float col[2][TB];
 };
+using DiagSmem = DiagSmemT<T>;
 
+template <int TM>
 __device__ __forceinline__ void diag_closure(float *__restrict__ D, int64_t ld,
                                              int32_t *__restrict__ P, int base, int m,
-                                             DiagSmem &sm) {
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int wy = w >> 1, wx = w & 1, ly = lane >> 3, lx = lane & 7;
+                                             DiagSmemT<16 * TM> &sm) {
+  const int ty = thread_ty(), tx = thread_tx();
   const float INF = inf<float>();
-  float d[8][8];
+  float d[TM][TM];
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr) {
-    const int i = row_of(rr, wy, ly);
+  for (int rr = 0; rr < TM; ++rr) {
+    const int i = row_at(rr, ty);
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      const int j = col_of(cc, wx, lx);
+    for (int cc = 0; cc < TM; ++cc) {
+      const int j = col_at(cc, tx);
       d[rr][cc] = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : INF;
     }
   }
   for (int k = 0; k < m; ++k) {
     const int buf = k & 1;
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr)
-      if (row_of(rr, wy, ly) == k) {
+    for (int rr = 0; rr < TM; ++rr)
+      if (row_at(rr, ty) == k) {
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) sm.row[buf][col_of(cc, wx, lx)] = d[rr][cc];
+        for (int cc = 0; cc < TM; ++cc) sm.row[buf][col_at(cc, tx)] = d[rr][cc];
       }
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc)
-      if (col_of(cc, wx, lx) == k) {
+    for (int cc = 0; cc < TM; ++cc)
+      if (col_at(cc, tx) == k) {
 #pragma unroll
-        for (int rr = 0; rr < 8; ++rr) sm.col[buf][row_of(rr, wy, ly)] = d[rr][cc];
+        for (int rr = 0; rr < TM; ++rr) sm.col[buf][row_at(rr, ty)] = d[rr][cc];
       }
     __syncthreads();
-    float a[8], b[8];
+    float a[TM], b[TM];
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) a[rr] = sm.col[buf][row_of(rr, wy, ly)];
+    for (int rr = 0; rr < TM; ++rr) a[rr] = sm.col[buf][row_at(rr, ty)];
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) b[cc] = sm.row[buf][col_of(cc, wx, lx)];
+    for (int cc = 0; cc < TM; ++cc) b[cc] = sm.row[buf][col_at(cc, tx)];
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      const int i = row_of(rr, wy, ly);
+    for (int rr = 0; rr < TM; ++rr) {
+      const int i = row_at(rr, ty);
 #pragma unroll
-      for (int cc = 0; cc < 8; ++cc) {
+      for (int cc = 0; cc < TM; ++cc) {
         const float cand = __fadd_rn(a[rr], b[cc]);
         if (cand < d[rr][cc]) {
           d[rr][cc] = cand;
-          if (P) P[(int64_t)(base + i) * ld + base + col_of(cc, wx, lx)] = base + k;
+          if (P) P[(int64_t)(base + i) * ld + base + col_at(cc, tx)] = base + k;
         }
       }
     }
   }
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr) {
-    const int i = row_of(rr, wy, ly);
+  for (int rr = 0; rr < TM; ++rr) {
+    const int i = row_at(rr, ty);
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      const int j = col_of(cc, wx, lx);
+    for (int cc = 0; cc < TM; ++cc) {
+      const int j = col_at(cc, tx);
       if (i < m && j < m) D[(int64_t)(base + i) * ld + base + j] = d[rr][cc];
     }
   }

@@ -29,7 +29,7 @@ def test_library_builds_loads_and_exports():
         assert hasattr(lib, name), name
     L = apsp.load()
     assert L.apsp_version() >= 100
-    assert L.apsp_fw_block_size(4) == 128 and L.apsp_fw_block_size(8) == 64
+    assert L.apsp_fw_block_size(4) == 128 and L.apsp_fw_block_size(8) == 128
     assert L.apsp_fw_block_size(2) == 0
     assert L.apsp_status_string(0) == b"APSP_OK"
     assert L.apsp_batched_num_classes() == 4

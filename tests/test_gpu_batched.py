@@ -113,3 +113,29 @@ def test_full_config_sampled_graphs():
         pairs = list(zip(rng.integers(0, n, 300).tolist(), rng.integers(0, n, 300).tolist()))
         assert oracle.check_paths(W, D, P, pairs=pairs) == 0
     plan.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_every_variant_is_exact(variant):
+    """Each kernel variant (block edge / register tile) solves every size class
+    exactly; the autotuner's choice can only change speed."""
+    saved = [B.get_variant(c) for c in range(B.num_classes())]
+    try:
+        for c in range(B.num_classes()):
+            B.set_variant(c, variant)
+        sizes = [1, 7, 63, 64, 65, 100, 128, 129, 191, 200, 256, 257, 320, 511]
+        mats = [graphgen.dense_graph(n, 0.3, 1200 + n) for n in sizes]
+        for W, (D, P) in zip(mats, _solve(sizes, mats)):
+            np.testing.assert_array_equal(D, oracle.fw(W)[0])
+            assert oracle.check_paths(W, D, P) == 0
+    finally:
+        for c, v in enumerate(saved):
+            B.set_variant(c, v)
+
+
+def test_autotuner_picks_a_variant_per_class():
+    from paper_2105_07298_gb300 import autotune
+    res = autotune.autotune(graphs_per_class=16, reps=1, save=False)
+    assert set(res) == set(range(B.num_classes()))
+    for c, r in res.items():
+        assert r["variant"] == int(np.argmin(r["ms"])) and B.get_variant(c) == r["variant"]

@@ -53,22 +53,55 @@ def test_integer_weights_bit_exact(n, dtype):
     assert oracle.check_paths(W, D, P) == 0
 
 
-@pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("n", [70, 200, 333])
-def test_real_weights_match_blocked_oracle_bitwise(n, dtype):
-    W = graphgen.dense_graph(n, 0.4, 77 + n, weights="real", lo=0.5, hi=2.0, dtype=dtype)
-    D, P, _ = _run(W, dtype)
-    TB = apsp.block_size(torch.float32 if dtype == np.float32 else torch.float64)
-    Db, Pb = oracle.bfw(W, TB)
+def test_real_weights_f32_match_blocked_oracle_bitwise(n):
+    """FP32 follows the paper's four phases exactly: same sums, same order of k."""
+    W = graphgen.dense_graph(n, 0.4, 77 + n, weights="real", lo=0.5, hi=2.0, dtype=np.float32)
+    D, P, _ = _run(W, np.float32)
+    Db, Pb = oracle.bfw(W, apsp.block_size(torch.float32))
     np.testing.assert_array_equal(D, Db)
     np.testing.assert_array_equal(P, Pb)
-    # and against the exact (FP64 classic) distances
     D64, _ = oracle.fw(W.astype(np.float64))
     fin = np.isfinite(D64)
     np.testing.assert_array_equal(np.isfinite(D), fin)
     rel = np.abs(D[fin].astype(np.float64) - D64[fin]) / np.maximum(np.abs(D64[fin]), 1e-300)
-    assert rel.max() <= (1e-5 if dtype == np.float32 else 1e-12), rel.max()
-    assert oracle.check_paths(W, D, P, rtol=1e-5 if dtype == np.float32 else 1e-12) == 0
+    assert rel.max() <= 1e-5, rel.max()
+    assert oracle.check_paths(W, D, P, rtol=1e-5) == 0
+
+
+@pytest.mark.parametrize("n,p", [(70, 0.4), (200, 0.4), (333, 0.4), (300, 0.05)])
+def test_real_weights_f64_within_1e12(n, p):
+    """FP64 (phases 2/3 through the closed diagonal block): within 1e-12 relative
+    of the exact FP64 distances; phase 1 and 4 candidate sums are IEEE FP64."""
+    W = graphgen.dense_graph(n, p, 177 + n, weights="real", lo=0.5, hi=2.0, dtype=np.float64)
+    D, P, _ = _run(W, np.float64)
+    D64, _ = oracle.fw(W)
+    fin = np.isfinite(D64)
+    np.testing.assert_array_equal(np.isfinite(D), fin)
+    rel = np.abs(D[fin] - D64[fin]) / np.maximum(np.abs(D64[fin]), 1e-300)
+    assert rel.max() <= 1e-12, rel.max()
+    assert oracle.check_paths(W, D, P, rtol=1e-12) == 0
+    assert apsp.device_status() == apsp.APSP_OK
+
+
+def test_f64_values_beyond_float_range_and_fractions():
+    """FP64 inputs FP32 cannot hold exactly (2^-30 fractions, magnitudes near 1e300,
+    tiny values): the interval filter must still give exact FP64 results."""
+    rng = np.random.default_rng(8)
+    n = 260
+    W = graphgen.dense_graph(n, 0.3, 99, dtype=np.float64)
+    fin = np.isfinite(W) & ~np.eye(n, dtype=bool)
+    W[fin] = W[fin] + rng.integers(0, 4, fin.sum()) * 2.0 ** -30
+    D, P, _ = _run(W, np.float64)
+    np.testing.assert_array_equal(D, oracle.fw(W)[0])  # dyadic sums: exact in FP64
+    for scale in (1e300, 1e-300):
+        Ws = np.where(np.isfinite(W), W * scale, np.inf)
+        np.fill_diagonal(Ws, 0)
+        D, P, _ = _run(Ws, np.float64)
+        Dref = oracle.fw(Ws)[0]
+        ok = np.isfinite(Dref)
+        np.testing.assert_array_equal(np.isfinite(D), ok)
+        np.testing.assert_allclose(D[ok], Dref[ok], rtol=1e-12)
 
 
 def test_config_small_n1024_full():
@@ -183,3 +216,20 @@ def test_full_size_sampled_rows(n, dtype):
             s += float(W_host[a, b])
         bad += int(s != dmap[i][j])
     assert bad == 0
+
+
+def test_phase_timing_hook_and_device_status():
+    """The timing hook brackets every launch (1 + 3R for FP32 with a path matrix)
+    and no bounded wait runs out on a normal solve."""
+    n = 1000
+    W = torch.from_numpy(graphgen.dense_graph(n, 0.3, 5)).to(DEV)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.profile_enable(True)
+    apsp.apsp_fw_f32(W, P)
+    prof = apsp.profile_collect()
+    apsp.profile_enable(False)
+    R = (n + 127) // 128
+    assert prof["path_init"][1] == 1
+    assert prof["phase1_diag"][1] == R and prof["phase2_panels"][1] == R and prof["phase3_minplus"][1] == R
+    assert all(ms >= 0 for ms, _ in prof.values())
+    assert apsp.device_status() == apsp.APSP_OK
