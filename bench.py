@@ -199,9 +199,10 @@ def phase3_relax_per_launch(n: int, T: int) -> float:
     return tot / R
 
 
-def workload_config(n: int, world: int) -> dict:
+def workload_config(n: int, world: int, dtype: str = "f32") -> dict:
+    prec = "FP64" if dtype == "f64" else "FP32"
     return {"workload": f"blocked FW, one dense directed graph per GPU, n={n}, edge prob 0.5, "
-                        "integer weights U[1,100], FP32 distances + int32 path matrix",
+                        f"integer weights U[1,100], {prec} distances + int32 path matrix",
             "n": n, "edge_prob": 0.5, "path_matrix": True,
             "l2": "inputs larger than L2 (4 GiB distances restored from a resident copy each step)",
             "parallelism": f"{world} independent graph(s), one per GPU"}
@@ -251,7 +252,9 @@ def run_reference(args):
     import oracle
     oracle.build()
     n = args.n
-    W = graphgen.dense_graph_torch(n, 0.5, SEED).numpy()
+    import torch
+    W = graphgen.dense_graph_torch(n, 0.5, SEED, dtype=torch.float64 if args.dtype == "f64"
+                                   else torch.float32).numpy()
     per_step = args.ref_step_seconds
     for _ in range(args.warmup):
         oracle_partial_rate(W, per_step / 4)
@@ -264,9 +267,9 @@ def run_reference(args):
     value = statistics.median(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic",
-            "config": workload_config(n, world),
+            "config": workload_config(n, world, args.dtype),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": f"outer k iterations 0..{min(ks)}-1 of classic FW (Algorithm 1) "
                                        f"on the n={n} graph per step (fixed per-call cost excluded)"},
@@ -277,15 +280,16 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def bench_fp32(torch, apsp, graphgen, args, rank, world, dev):
+def bench_main(torch, apsp, graphgen, args, rank, world, dev):
     n = args.n
-    W = graphgen.dense_graph_torch(n, 0.5, SEED + rank, device=dev)
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    W = graphgen.dense_graph_torch(n, 0.5, SEED + rank, dtype=dt, device=dev)
     D = torch.empty_like(W)
     P = torch.empty((n, n), dtype=torch.int32, device=dev)
 
     def step():
         D.copy_(W)
-        apsp.apsp_fw_f32(D, P)
+        apsp.apsp_fw(D, P)
 
     for _ in range(args.warmup):
         step()
@@ -463,18 +467,21 @@ def run_ours(args):
     peaks = measured_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
 
-    W, D, P, t, prof, clocks = bench_fp32(torch, apsp, graphgen, args, rank, world, dev)
+    W, D, P, t, prof, clocks = bench_main(torch, apsp, graphgen, args, rank, world, dev)
     n = args.n
     t_max = reduce_max(t, world, dev)
     total_relax = reduce_sum(float(n) ** 3 * args.steps, world, dev)
     value = total_relax / t_max
 
-    T = apsp.block_size(torch.float32)
+    T = apsp.block_size(torch.float64 if args.dtype == "f64" else torch.float32)
     k3_ms, k3_launches = prof["phase3_minplus"]
     per_launch_s = (k3_ms / 1e3) / max(k3_launches, 1)
     relax_launch = phase3_relax_per_launch(n, T)
     achieved = 2 * relax_launch / per_launch_s / 1e12  # Eq. 1 FLOP/s (add + compare)
-    peak = 2 * alu_peak_relax_per_s(facts["sms"], max_mhz) / 1e12
+    # FP64 runs two FP32 interval relaxations (lower and upper bound) per FP64
+    # relaxation on the same pipes: its bound is half the FP32 add+min peak.
+    per_clk = 64.0 if args.dtype == "f64" else 128.0
+    peak = 2 * alu_peak_relax_per_s(facts["sms"], max_mhz) * per_clk / 128.0 / 1e12
     mhz_meas = clocks["sm_mhz"] if clocks else None
     traffic = profiled_traffic(n)
     launches = sum(c for _, c in prof.values())
@@ -483,16 +490,17 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(n, world),
-        "roofline": {"bound": "alu", "kernel": "fw_phase3_minplus_f32 (phase 4)", "block": T,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": workload_config(n, world, args.dtype),
+        "roofline": {"bound": "alu", "block": T,
+                     "kernel": "fw64_product<0> (phase 4)" if args.dtype == "f64" else "fw_phase3_minplus_f32 (phase 4)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic,
                      "flop_def": "Eq. 1: 2 FLOP (add + compare) per relaxation; "
                                  f"{relax_launch:.4e} relaxations per launch (average over rounds)",
-                     "peak_basis": f"{facts['sms']} SMs x 128 relax/clk/SM x {max_mhz:.0f} MHz (max SM clock)",
-                     "frac_at_measured_clock": (achieved / (2 * alu_peak_relax_per_s(facts['sms'], mhz_meas) / 1e12)
-                                                if mhz_meas else None),
+                     "peak_basis": f"{facts['sms']} SMs x {per_clk:.0f} relax/clk/SM x {max_mhz:.0f} MHz (max SM clock)",
+                     "frac_at_measured_clock": (achieved / (2 * alu_peak_relax_per_s(facts['sms'], mhz_meas)
+                                                            * per_clk / 128.0 / 1e12) if mhz_meas else None),
                      "avg_launch_ms": per_launch_s * 1e3, "launches": k3_launches},
         "phase_time_ms": phase_share,
         "gpu_launches": launches,
@@ -500,7 +508,7 @@ def run_ours(args):
         "device": facts,
     }
 
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and args.dtype == "f32":
         del D
         torch.cuda.empty_cache()
         e2e_value, h2d, d2h, Wh = bench_e2e(torch, apsp, graphgen, W, args)
@@ -539,6 +547,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32",
+                    help="precision of the timed single-graph solve (the headline is f32)")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--fp64-n", type=int, default=32768)
     ap.add_argument("--fp64-steps", type=int, default=1)

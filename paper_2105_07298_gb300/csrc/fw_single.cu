@@ -277,41 +277,61 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
   __syncthreads();
   const float *acp = pan.Acp + (int64_t)I * T * T;
   const float *bt = pan.Bt + (int64_t)J * T * T;
-  const int w = tid >> 5, j0 = 4 * lane;
-#pragma unroll 1
-  for (int i = w * 16; i < w * 16 + 16; ++i) {
-    if (i >= mI) break;
-    const float4 c = *reinterpret_cast<const float4 *>(&Cs[i * T + j0]);
-    float *row = D + (int64_t)(baseI + i) * ld + baseJ;
-    const float cv[4] = {c.x, c.y, c.z, c.w};
-    float ov[4] = {INF, INF, INF, INF};
-    if (vec_ok && j0 + 3 < mJ) {
-      const float4 o = *reinterpret_cast<const float4 *>(row + j0);
-      ov[0] = o.x; ov[1] = o.y; ov[2] = o.z; ov[3] = o.w;
-    } else {
+  const int w = tid >> 5, j0 = 4 * lane, i0 = w * 16;
+  const bool vec = vec_ok && j0 + 3 < mJ;
+  // Pass 1 (unrolled): all 16 old rows of the warp are loaded before any is
+  // used (one memory round trip), improvements are flagged and written.
+  float4 o[16];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (j0 + q < mJ) ov[q] = row[j0 + q];
-    }
-    unsigned imp = 0u;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (j0 + q < mJ && cv[q] < ov[q]) imp |= 1u << q;
-    if (imp) {
-      if (vec_ok && j0 + 3 < mJ) {
-        *reinterpret_cast<float4 *>(row + j0) =
-            make_float4(imp & 1 ? cv[0] : ov[0], imp & 2 ? cv[1] : ov[1], imp & 4 ? cv[2] : ov[2],
-                        imp & 8 ? cv[3] : ov[3]);
+  for (int t = 0; t < 16; ++t) {
+    const float *row = D + (int64_t)(baseI + i0 + t) * ld + baseJ;
+    o[t] = make_float4(INF, INF, INF, INF);
+    if (i0 + t < mI) {
+      if (vec) {
+        o[t] = *reinterpret_cast<const float4 *>(row + j0);
       } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (imp >> q & 1) row[j0 + q] = cv[q];
+        if (j0 < mJ) o[t].x = row[j0];
+        if (j0 + 1 < mJ) o[t].y = row[j0 + 1];
+        if (j0 + 2 < mJ) o[t].z = row[j0 + 2];
+        if (j0 + 3 < mJ) o[t].w = row[j0 + 3];
       }
     }
-    if (!P) continue;
-    // P: one improved output per warp pass; lane l tests k = 4l..4l+3.
+  }
+  unsigned long long flags = 0ull;  // bit 4t + q: row i0 + t, column j0 + q improved
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    if (i0 + t >= mI) continue;
+    const float4 c = *reinterpret_cast<const float4 *>(&Cs[(i0 + t) * T + j0]);
+    unsigned imp = 0u;
+    if (j0 < mJ && c.x < o[t].x) imp |= 1u;
+    if (j0 + 1 < mJ && c.y < o[t].y) imp |= 2u;
+    if (j0 + 2 < mJ && c.z < o[t].z) imp |= 4u;
+    if (j0 + 3 < mJ && c.w < o[t].w) imp |= 8u;
+    if (!imp) continue;
+    flags |= (unsigned long long)imp << (4 * t);
+    float *row = D + (int64_t)(baseI + i0 + t) * ld + baseJ;
+    if (vec) {
+      *reinterpret_cast<float4 *>(row + j0) = make_float4(imp & 1 ? c.x : o[t].x, imp & 2 ? c.y : o[t].y,
+                                                          imp & 4 ? c.z : o[t].z, imp & 8 ? c.w : o[t].w);
+    } else {
+      if (imp & 1) row[j0] = c.x;
+      if (imp & 2) row[j0 + 1] = c.y;
+      if (imp & 4) row[j0 + 2] = c.z;
+      if (imp & 8) row[j0 + 3] = c.w;
+    }
+  }
+  if (!P) return;
+  // Pass 2 (rolled): P for each improved output, one per warp pass; lane l
+  // tests k = 4l..4l+3 of the round (A row and B column, contiguous copies).
+  unsigned long long wflags = __reduce_or_sync(kFullMask, (unsigned)(flags >> 32)) ;
+  wflags = (wflags << 32) | __reduce_or_sync(kFullMask, (unsigned)flags);
+#pragma unroll 1
+  while (wflags) {
+    const int t = (__ffsll((long long)wflags) - 1) >> 2;
+    wflags &= ~(0xfull << (4 * t));
+    const int i = i0 + t;
+    unsigned imp = (unsigned)(flags >> (4 * t)) & 0xfu;
     unsigned bal = __ballot_sync(kFullMask, imp != 0);
-    if (!bal) continue;
     const float4 av = reinterpret_cast<const float4 *>(acp + i * T)[lane];
     while (bal) {
       const int src = __ffs(bal) - 1;

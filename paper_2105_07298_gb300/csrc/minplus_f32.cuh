@@ -36,11 +36,21 @@ constexpr int T = 128;        // block edge of the TM = 8 configuration
 template <int TB>
 union SmemT {
   struct {
-    unsigned long long As[KP][TB];
-    unsigned long long Bs[KP][TB];
+    unsigned long long As[2][KP][TB];  // two slab buffers (cp.async double buffering)
+    unsigned long long Bs[2][KP][TB];
   };
   float Cs[TB][TB];  // epilogue: the block of new candidates
 };
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 using Smem = SmemT<T>;
 
 // Thread (warp w, lane l): ty = (w/2)*4 + l/8 (0..15), tx = (w%2)*8 + l%8
@@ -111,64 +121,53 @@ __device__ __forceinline__ void block_product(float *__restrict__ D, int64_t ld,
 #pragma unroll
     for (int c = 0; c < TM; ++c) acc[a][c] = INF;
 
-  for (int k0 = 0; k0 < mK; k0 += KS) {
-    __syncthreads();  // previous slab (or previous use of sm) fully consumed
-    // A slab: TB rows x 32 k; a float4 along k gives two pairs
+  // Slab staging: every element is one 4-byte asynchronous copy straight into
+  // its place in the k-pair layout (As[kp][i] = (A[i][2kp], A[i][2kp+1]),
+  // Bs[kp][j] = (B[2kp][j], B[2kp+1][j])); entries outside the matrix get +inf
+  // by a plain store.  Two buffers: slab s+1 is in flight while s is used.
+  auto stage = [&](int k0, int buf) {
+    float *as = reinterpret_cast<float *>(&sm.As[buf][0][0]);
+    float *bs = reinterpret_cast<float *>(&sm.Bs[buf][0][0]);
 #pragma unroll
-    for (int q = 0; q < (TB * KS / 4) / THREADS; ++q) {
-      const int idx = tid + q * THREADS;
-      const int i = idx >> 3, k4 = (idx & 7) * 4;
-      const int kk = k0 + k4;
-      float v[4];
-      const float *src = D + (int64_t)(baseI + i) * ld + baseK + kk;
-      if (vec_ok && i < mI && kk + 3 < mK) {
-        const float4 t = *reinterpret_cast<const float4 *>(src);
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (i < mI && kk + u < mK) ? src[u] : INF;
-      }
-      sm.As[k4 / 2][i] = pack2(v[0], v[1]);
-      sm.As[k4 / 2 + 1][i] = pack2(v[2], v[3]);
+    for (int q = 0; q < TB * KS / THREADS; ++q) {  // A: lanes walk k along a row
+      const int idx = tid + q * THREADS, i = idx / KS, k = idx % KS;
+      float *dst = as + ((k >> 1) * TB + i) * 2 + (k & 1);
+      if (i < mI && k0 + k < mK) cp_async4(dst, D + (int64_t)(baseI + i) * ld + baseK + k0 + k);
+      else *dst = INF;
     }
-    // B slab: rows k and k+1 over TB columns -> pairs
 #pragma unroll
-    for (int q = 0; q < (KP * TB / 4) / THREADS; ++q) {
-      const int idx = tid + q * THREADS;
-      const int kp = idx / (TB / 4), j4 = (idx % (TB / 4)) * 4;
-      const int kk = k0 + 2 * kp;
-      float v0[4], v1[4];
-      const float *s0 = D + (int64_t)(baseK + kk) * ld + baseJ + j4;
-      const float *s1 = s0 + ld;
-      if (vec_ok && j4 + 3 < mJ && kk + 1 < mK) {
-        const float4 t0 = *reinterpret_cast<const float4 *>(s0);
-        const float4 t1 = *reinterpret_cast<const float4 *>(s1);
-        v0[0] = t0.x; v0[1] = t0.y; v0[2] = t0.z; v0[3] = t0.w;
-        v1[0] = t1.x; v1[1] = t1.y; v1[2] = t1.z; v1[3] = t1.w;
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          v0[u] = (j4 + u < mJ && kk < mK) ? s0[u] : INF;
-          v1[u] = (j4 + u < mJ && kk + 1 < mK) ? s1[u] : INF;
-        }
-      }
-      ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&sm.Bs[kp][j4]);
-      dst[0] = make_ulonglong2(pack2(v0[0], v1[0]), pack2(v0[1], v1[1]));
-      dst[1] = make_ulonglong2(pack2(v0[2], v1[2]), pack2(v0[3], v1[3]));
+    for (int q = 0; q < KS * TB / THREADS; ++q) {  // B: lanes walk j along a row
+      const int idx = tid + q * THREADS, k = idx / TB, j = idx % TB;
+      float *dst = bs + ((k >> 1) * TB + j) * 2 + (k & 1);
+      if (j < mJ && k0 + k < mK) cp_async4(dst, D + (int64_t)(baseK + k0 + k) * ld + baseJ + j);
+      else *dst = INF;
     }
-    __syncthreads();
+    cp_async_commit();
+  };
+  const int nslab = (mK + KS - 1) / KS;
+  __syncthreads();  // the previous user of sm is done with it
+  stage(0, 0);
+  for (int s = 0; s < nslab; ++s) {
+    const int buf = s & 1;
+    if (s + 1 < nslab) {
+      stage((s + 1) * KS, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // slab s visible to every thread
 #pragma unroll 1
     for (int kp = 0; kp < KP; ++kp) {
       unsigned long long a[TM], b[TM];
 #pragma unroll
       for (int rr = 0; rr < TM; rr += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[kp][row_at(rr, ty)]);
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[buf][kp][row_at(rr, ty)]);
         a[rr] = t.x;
         a[rr + 1] = t.y;
       }
 #pragma unroll
       for (int cc = 0; cc < TM; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[kp][col_at(cc, tx)]);
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[buf][kp][col_at(cc, tx)]);
         b[cc] = t.x;
         b[cc + 1] = t.y;
       }
@@ -177,6 +176,7 @@ __device__ __forceinline__ void block_product(float *__restrict__ D, int64_t ld,
 #pragma unroll
         for (int cc = 0; cc < TM; ++cc) relax2(acc[rr][cc], a[rr], b[cc]);
     }
+    __syncthreads();  // slab s consumed before its buffer is refilled
   }
 
   // Epilogue.  The new candidates go to shared memory; then each warp owns
@@ -193,55 +193,65 @@ __device__ __forceinline__ void block_product(float *__restrict__ D, int64_t ld,
       *reinterpret_cast<float2 *>(&sm.Cs[row_at(rr, ty)][col_at(cc, tx)]) =
           make_float2(acc[rr][cc], acc[rr][cc + 1]);
   __syncthreads();
-  const int w = tid >> 5, j0 = CPL * lane;
-  unsigned long long flags = 0ull;  // bit (t * CPL + q): row w*RPW + t, column j0 + q
-#pragma unroll 1
-  for (int t = 0; t < RPW; ++t) {
-    const int i = w * RPW + t;
-    if (i >= mI) break;
-    const float *row = D + (int64_t)(baseI + i) * ld + baseJ;
-    unsigned imp = 0u;
+  const int w = tid >> 5, j0 = CPL * lane, i0 = w * RPW;
+  // Pass 1 (unrolled): every old value of the warp's rows is loaded before
+  // any is used (one memory round trip), then the improvements are flagged.
+  float o[RPW][CPL];
+#pragma unroll
+  for (int t = 0; t < RPW; ++t)
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
-      if (j0 + q < mJ && sm.Cs[i][j0 + q] < row[j0 + q]) imp |= 1u << q;
-    flags |= (unsigned long long)imp << (t * CPL);
-    if (!P) continue;
-    unsigned bal = __ballot_sync(kFullMask, imp != 0);
-    if (!bal) continue;
-    const float *arow = D + (int64_t)(baseI + i) * ld + baseK;
-    float av[CPL];
+      o[t][q] = (i0 + t < mI && j0 + q < mJ) ? D[(int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q] : INF;
+  unsigned long long flags = 0ull;  // bit (t * CPL + q): row i0 + t, column j0 + q
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) av[q] = (j0 + q < mK) ? arow[j0 + q] : INF;
-    while (bal) {
-      const int src = __ffs(bal) - 1;
-      const unsigned sim = __shfl_sync(kFullMask, imp, src);
-      const int q0 = __ffs(sim) - 1;
-      if (lane == src) imp &= imp - 1;
-      if (!(sim & (sim - 1))) bal &= bal - 1;
-      const int sj = CPL * src + q0;
-      const float tgt = sm.Cs[i][sj];
-      const float *bcol = D + (int64_t)baseK * ld + baseJ + sj;
-      unsigned h = 0u;
+  for (int t = 0; t < RPW; ++t)
 #pragma unroll
-      for (int q = 0; q < CPL; ++q)
-        if (j0 + q < mK && __fadd_rn(av[q], bcol[(int64_t)(j0 + q) * ld]) == tgt) h |= 1u << q;
-      const unsigned hb = __ballot_sync(kFullMask, h != 0);
-      const int L = __ffs(hb) - 1;
-      const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
-      if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj] = baseK + CPL * L + (__ffs(hL) - 1);
+    for (int q = 0; q < CPL; ++q)
+      if (sm.Cs[i0 + t][j0 + q] < o[t][q]) flags |= 1ull << (t * CPL + q);
+  // Pass 2 (rolled): P for each improved output, one per warp pass; lane l
+  // tests k = CPL*l .. CPL*l + CPL-1, reading A and B from global memory.
+  if (P) {
+    unsigned long long wflags = __reduce_or_sync(kFullMask, (unsigned)(flags >> 32));
+    wflags = (wflags << 32) | __reduce_or_sync(kFullMask, (unsigned)flags);
+    constexpr unsigned long long kRowMask = (1ull << CPL) - 1;
+#pragma unroll 1
+    while (wflags) {
+      const int t = (__ffsll((long long)wflags) - 1) / CPL;
+      wflags &= ~(kRowMask << (t * CPL));
+      const int i = i0 + t;
+      unsigned imp = (unsigned)(flags >> (t * CPL)) & (unsigned)kRowMask;
+      unsigned bal = __ballot_sync(kFullMask, imp != 0);
+      const float *arow = D + (int64_t)(baseI + i) * ld + baseK;
+      float av[CPL];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) av[q] = (j0 + q < mK) ? arow[j0 + q] : INF;
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        const unsigned sim = __shfl_sync(kFullMask, imp, src);
+        const int q0 = __ffs(sim) - 1;
+        if (lane == src) imp &= imp - 1;
+        if (!(sim & (sim - 1))) bal &= bal - 1;
+        const int sj = CPL * src + q0;
+        const float tgt = sm.Cs[i][sj];
+        const float *bcol = D + (int64_t)baseK * ld + baseJ + sj;
+        unsigned h = 0u;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+          if (j0 + q < mK && __fadd_rn(av[q], bcol[(int64_t)(j0 + q) * ld]) == tgt) h |= 1u << q;
+        const unsigned hb = __ballot_sync(kFullMask, h != 0);
+        const int L = __ffs(hb) - 1;
+        const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
+        if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj] = baseK + CPL * L + (__ffs(hL) - 1);
+      }
     }
   }
   __syncthreads();  // every read of A and B (staging and recovery) precedes the writes
-#pragma unroll 1
-  for (int t = 0; t < RPW; ++t) {
-    const unsigned imp = (unsigned)(flags >> (t * CPL)) & ((1u << CPL) - 1);
-    if (!imp) continue;
-    const int i = w * RPW + t;
-    float *row = D + (int64_t)(baseI + i) * ld + baseJ;
+  // Pass 3: write the improved outputs.
+#pragma unroll
+  for (int t = 0; t < RPW; ++t)
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
-      if (imp >> q & 1) row[j0 + q] = sm.Cs[i][j0 + q];
-  }
+      if ((flags >> (t * CPL + q)) & 1ull) D[(int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q] = sm.Cs[i0 + t][j0 + q];
 }
 
 // Register-resident classic FW (Algorithm 1, strict "<") on the diagonal
