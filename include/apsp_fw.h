@@ -115,6 +115,28 @@ int apsp_fw_batched_run_f32(const apsp_batched_plan *plan, float *d_dist, int32_
 int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_t *h_n, const int64_t *h_off,
                         int32_t num_graphs, void *stream);
 
+/* No-allocation form of apsp_fw_batched_f32.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory at
+ * call time (a serving loop that forbids cudaMalloc on its hot path, code
+ * whose device memory comes from an allocator CUDA does not own, or an
+ * embedding where any hidden allocation is an error).  It allocates nothing:
+ * no cudaMalloc/cudaFree, no stream-ordered or library allocation, no host
+ * heap.  Its work list lives in one fixed device array of the library
+ * (1 MiB + 16 bytes, held on every GPU that loads the library until exit),
+ * so num_graphs may be at most 65536; larger batches return
+ * APSP_EUNSUPPORTED before anything is enqueued.  Arguments and results are
+ * those of apsp_fw_batched_f32 (same kernels, same results).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture on the device.  Every call shares the
+ * array and it keeps the last call's contents (each call resets what must
+ * start at zero); calls that overlap on the GPU (different streams or host
+ * threads) race on it, so the caller must serialise them.  h_n and h_off are
+ * read by asynchronous host-to-device copies on `stream`. */
+int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, const int32_t *h_n,
+                                const int64_t *h_off, int32_t num_graphs, void *stream);
+
 /* Autotuner hook for the batched kernel: per size class (0..3, vertex-count
  * bounds given by apsp_batched_class_bounds) pick the variant index used by
  * later plans.  apsp_batched_num_variants reports how many variants a class

@@ -33,6 +33,7 @@ SIGNATURES = {
     "apsp_batched_plan_destroy": (ctypes.c_int, [_p]),
     "apsp_fw_batched_run_f32": (ctypes.c_int, [_p, _p, _p, _p]),
     "apsp_fw_batched_f32": (ctypes.c_int, [_p, _p, _p, _p, _i32, _p]),
+    "apsp_fw_batched_f32_noalloc": (ctypes.c_int, [_p, _p, _p, _p, _i32, _p]),
     "apsp_batched_num_classes": (ctypes.c_int, []),
     "apsp_batched_class_bounds": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "apsp_batched_num_variants": (ctypes.c_int, [ctypes.c_int]),

@@ -288,3 +288,95 @@ APSP_EXPORT int apsp_batched_get_variant(int cls) {
   return (cls < 0 || cls >= apsp::kNumClasses) ? -1 : apsp::g_variant[cls];
 }
 
+// ---------------------------------------------------------------------------
+// No-allocation batched entry point (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory at call time: a serving loop
+// that forbids cudaMalloc on its hot path, code whose device memory comes
+// from an allocator CUDA does not own, or a library embedded where any hidden
+// allocation is an error.  This entry point takes the work list (counter,
+// largest-first order, sizes, offsets) from one file-scope device array of
+// fixed size instead of allocating it, and builds the order on the GPU, so it
+// allocates nothing, on the device or on the host.
+//
+// The array (1 MiB + 16 bytes, up to kNoAllocMaxGraphs graphs) is held by
+// every GPU that loads the library until the process exits.  Host code cannot
+// pass the array's name to a kernel (in host code it is only a stand-in, not
+// a device address): the first call on each device looks its address up with
+// cudaGetSymbolAddress while that device is current and caches it.  All calls
+// share the array and it keeps the previous call's contents; each call
+// resets the counter it needs.  Calls that overlap on the GPU (other streams,
+// other host threads) race on the array and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace apsp {
+
+constexpr int kNoAllocMaxGraphs = 65536;
+constexpr size_t kNoAllocBytes = 16 + (size_t)kNoAllocMaxGraphs * (4 + 4 + 8);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static unsigned char *g_noalloc_addr[64];  // device address of g_noalloc_scratch, per device
+
+// One CTA: counting sort of the graphs by decreasing size (ties in any
+// order), each entry tagged with its class's variant; also resets the work
+// counter.
+__global__ void __launch_bounds__(1024)
+    fw_batched_order(const int32_t *__restrict__ ns, int num, int32_t *__restrict__ order,
+                     int *__restrict__ counter, int v0, int v1, int v2, int v3) {
+  __shared__ int start[kBatchedMaxN + 2];
+  for (int v = threadIdx.x; v < kBatchedMaxN + 2; v += blockDim.x) start[v] = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < num; g += blockDim.x) atomicAdd(&start[ns[g]], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive scan from the largest size down
+    int run = 0;
+    for (int v = kBatchedMaxN; v >= 1; --v) {
+      const int c = start[v];
+      start[v] = run;
+      run += c;
+    }
+    *counter = 0;
+  }
+  __syncthreads();
+  const int var[kNumClasses] = {v0, v1, v2, v3};
+  for (int g = threadIdx.x; g < num; g += blockDim.x) {
+    const int n = ns[g];
+    order[atomicAdd(&start[n], 1)] = g | (var[class_of_n(n)] << 30);
+  }
+}
+
+}  // namespace apsp
+
+APSP_EXPORT int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, const int32_t *h_n,
+                                            const int64_t *h_off, int32_t num, void *stream) {
+  int st = validate(h_n, h_off, num);
+  if (st) return st;
+  if (num > apsp::kNoAllocMaxGraphs) return APSP_EUNSUPPORTED;
+  if (num == 0) return APSP_OK;
+  if (!d_dist) return APSP_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ECUDA;
+  if (!apsp::g_noalloc_addr[dev]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, apsp::g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return APSP_ECUDA;
+    }
+    apsp::g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
+  }
+  unsigned char *base = apsp::g_noalloc_addr[dev];
+  int *d_counter = reinterpret_cast<int *>(base);
+  int32_t *d_order = reinterpret_cast<int32_t *>(base + 16);
+  int32_t *d_n = d_order + apsp::kNoAllocMaxGraphs;
+  int64_t *d_off = reinterpret_cast<int64_t *>(d_n + apsp::kNoAllocMaxGraphs);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int grid = grid_for(num);
+  if (grid <= 0) return APSP_ECUDA;
+  cudaGetLastError();
+  cudaError_t e = cudaMemcpyAsync(d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return APSP_ECUDA;
+  apsp::fw_batched_order<<<1, 1024, 0, s>>>(d_n, num, d_order, d_counter, apsp::g_variant[0],
+                                            apsp::g_variant[1], apsp::g_variant[2], apsp::g_variant[3]);
+  apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
+      d_dist, d_path, d_order, d_n, d_off, num, d_counter);
+  return apsp::status_from(cudaGetLastError());
+}
