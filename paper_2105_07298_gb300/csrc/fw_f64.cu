@@ -326,41 +326,38 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       return;
     }
+    // Hand-pipelined operand loads: the hi operands of k-pair kp load while
+    // its lo products run, and the lo operands of kp+1 while its hi products
+    // run (two named operand sets; the compiler's unrolling would spill).
+    unsigned long long al[4], bl[8], ah[4], bh[8];
+    auto load_set = [&](int kp, const unsigned long long (*As)[T], const unsigned long long (*Bs)[T],
+                        unsigned long long (&a)[4], unsigned long long (&b)[8]) {
+#pragma unroll
+      for (int rr = 0; rr < 4; rr += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&As[kp][row4(rr, wy, ly)]);
+        a[rr] = t.x;
+        a[rr + 1] = t.y;
+      }
+#pragma unroll
+      for (int cc = 0; cc < 8; cc += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bs[kp][col8(cc, wx, lx)]);
+        b[cc] = t.x;
+        b[cc + 1] = t.y;
+      }
+    };
+    load_set(0, sm.Alo[st], sm.Blo[st], al, bl);
 #pragma unroll 1
     for (int kp = 0; kp < KP; ++kp) {
-      unsigned long long a[4], b[8];
-#pragma unroll
-      for (int rr = 0; rr < 4; rr += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Alo[st][kp][row4(rr, wy, ly)]);
-        a[rr] = t.x;
-        a[rr + 1] = t.y;
-      }
-#pragma unroll
-      for (int cc = 0; cc < 8; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Blo[st][kp][col8(cc, wx, lx)]);
-        b[cc] = t.x;
-        b[cc + 1] = t.y;
-      }
+      load_set(kp, sm.Ahi[st], sm.Bhi[st], ah, bh);
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) relax2_rm(lo[rr][cc], a[rr], b[cc]);
-#pragma unroll
-      for (int rr = 0; rr < 4; rr += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Ahi[st][kp][row4(rr, wy, ly)]);
-        a[rr] = t.x;
-        a[rr + 1] = t.y;
-      }
-#pragma unroll
-      for (int cc = 0; cc < 8; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bhi[st][kp][col8(cc, wx, lx)]);
-        b[cc] = t.x;
-        b[cc + 1] = t.y;
-      }
+        for (int cc = 0; cc < 8; ++cc) relax2_rm(lo[rr][cc], al[rr], bl[cc]);
+      if (kp + 1 < KP) load_set(kp + 1, sm.Alo[st], sm.Blo[st], al, bl);
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) relax2_rp(up[rr][cc], a[rr], b[cc]);
+        for (int cc = 0; cc < 8; ++cc) relax2_rp(up[rr][cc], ah[rr], bh[cc]);
     }
     __syncthreads();
     if (tid == 0 && s + STAGES < nslab) {

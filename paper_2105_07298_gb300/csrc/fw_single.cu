@@ -232,25 +232,41 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
       }
       return;
     }
-#pragma unroll 1  // no cross-iteration prefetch: keeps the kernel at <= 128 registers, no spills
-    for (int kp = 0; kp < KP; ++kp) {
-      unsigned long long a[8], b[8];
-#pragma unroll
-      for (int rr = 0; rr < 8; rr += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[st][kp][row_at(rr, ty)]);
-        a[rr] = t.x;
-        a[rr + 1] = t.y;
-      }
+    // Operand loads are software-pipelined by hand (the compiler's own
+    // unrolling would exceed 128 registers): the B pairs of k-pair kp+1 load
+    // while kp computes (two named buffers, k-pairs processed two at a time),
+    // and each A row-pair loads one row-pair ahead of its use.
+    const unsigned long long *Asl = &sm.As[st][0][0];
+    const unsigned long long *Bsl = &sm.Bs[st][0][0];
+    auto load_b = [&](int kp, unsigned long long (&b)[8]) {
 #pragma unroll
       for (int cc = 0; cc < 8; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[st][kp][col_at(cc, tx)]);
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bsl[kp * T + col_at(cc, tx)]);
         b[cc] = t.x;
         b[cc + 1] = t.y;
       }
+    };
+    auto compute = [&](int kp, const unsigned long long (&b)[8]) {
+      ulonglong2 an = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(0, ty)]);
 #pragma unroll
-      for (int rr = 0; rr < 8; ++rr)
+      for (int rp = 0; rp < 4; ++rp) {
+        const ulonglong2 ac = an;
+        if (rp < 3) an = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(2 * rp + 2, ty)]);
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) mp32::relax2(acc[rr][cc], a[rr], b[cc]);
+        for (int cc = 0; cc < 8; ++cc) {
+          mp32::relax2(acc[2 * rp][cc], ac.x, b[cc]);
+          mp32::relax2(acc[2 * rp + 1][cc], ac.y, b[cc]);
+        }
+      }
+    };
+    unsigned long long b0[8], b1[8];
+    load_b(0, b0);
+#pragma unroll 1
+    for (int kp = 0; kp < KP; kp += 2) {
+      load_b(kp + 1, b1);
+      compute(kp, b0);
+      if (kp + 2 < KP) load_b(kp + 2, b0);
+      compute(kp + 1, b1);
     }
     __syncthreads();  // stage st fully read
     if (tid == 0 && s + STAGES < nslab) {
