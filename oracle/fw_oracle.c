@@ -220,20 +220,25 @@ EXPORT int oracle_bellman_ford_f64(const double *W, int64_t n, int64_t src, doub
  * Path reconstruction from P: path(i,j) = [i, j] if P[i][j] = -1, else
  * path(i,k) ++ path(k,j) without repeating k.  Writes the vertex sequence
  * (i first, j last) into out and returns its length, or -1 if it exceeds
- * max_len (which a correct P never does for max_len >= n).
+ * max_len (which a correct P never does for max_len >= n) or P does not
+ * encode a path (a split index outside 0..ld-1, or a split that never ends).
  * ------------------------------------------------------------------------- */
 static int64_t walk(const int32_t *P, int64_t ld, int64_t i, int64_t j, int64_t *out,
-                    int64_t len, int64_t max_len) {
-  /* appends the vertices after i up to and including j */
+                    int64_t len, int64_t max_len, int64_t depth) {
+  /* appends the vertices after i up to and including j; a valid P splits a
+   * path of at most max_len vertices at most max_len levels deep, so deeper
+   * recursion or an index outside 0..ld-1 means P encodes no path */
+  if (depth > max_len) return -1;
   const int32_t k = P[i * ld + j];
   if (k < 0) {
     if (len >= max_len) return -1;
     out[len] = j;
     return len + 1;
   }
-  len = walk(P, ld, i, k, out, len, max_len);
+  if (k >= ld) return -1;
+  len = walk(P, ld, i, k, out, len, max_len, depth + 1);
   if (len < 0) return -1;
-  return walk(P, ld, k, j, out, len, max_len);
+  return walk(P, ld, k, j, out, len, max_len, depth + 1);
 }
 
 EXPORT int64_t oracle_reconstruct_path(const int32_t *P, int64_t ld, int64_t i, int64_t j,
@@ -241,7 +246,7 @@ EXPORT int64_t oracle_reconstruct_path(const int32_t *P, int64_t ld, int64_t i, 
   if (max_len < 1) return -1;
   out[0] = i;
   if (i == j) return 1;
-  return walk(P, ld, i, j, out, 1, max_len);
+  return walk(P, ld, i, j, out, 1, max_len, 0);
 }
 
 /* -------------------------------------------------------------------------
