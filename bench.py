@@ -483,6 +483,10 @@ def run_ours(args):
     per_clk = 64.0 if args.dtype == "f64" else 128.0
     peak = 2 * alu_peak_relax_per_s(facts["sms"], max_mhz) * per_clk / 128.0 / 1e12
     mhz_meas = clocks["sm_mhz"] if clocks else None
+    try:  # the inner-loop instruction pair on registers only, this GPU (relax/clk/SM)
+        rate_meas = apsp.measure_peak(8 if args.dtype == "f64" else 4)
+    except Exception:
+        rate_meas = None
     traffic = profiled_traffic(n)
     launches = sum(c for _, c in prof.values())
     phase_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}
@@ -501,7 +505,10 @@ def run_ours(args):
                      "peak_basis": f"{facts['sms']} SMs x {per_clk:.0f} relax/clk/SM x {max_mhz:.0f} MHz (max SM clock)",
                      "frac_at_measured_clock": (achieved / (2 * alu_peak_relax_per_s(facts['sms'], mhz_meas)
                                                             * per_clk / 128.0 / 1e12) if mhz_meas else None),
-                     "avg_launch_ms": per_launch_s * 1e3, "launches": k3_launches},
+                     "avg_launch_ms": per_launch_s * 1e3, "launches": k3_launches,
+                     "measured_pair_rate_relax_per_clk_sm": rate_meas,
+                     "frac_of_measured_pair_rate": (achieved / (2 * rate_meas * facts["sms"] * max_mhz * 1e6 / 1e12)
+                                                    if rate_meas else None)},
         "phase_time_ms": phase_share,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -42,6 +42,7 @@ SIGNATURES = {
     "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
     "apsp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "apsp_device_status": (ctypes.c_int, [_p]),
+    "apsp_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _p]),
     "apsp_profile_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
 }
 
@@ -145,6 +146,13 @@ def apsp_fw(dist, path=None, stream=None):
 def device_status(stream=None) -> int:
     """Synchronize the stream; return (and clear) the kernels' device-side error word."""
     return int(load().apsp_device_status(_stream_ptr(stream)))
+
+
+def measure_peak(dtype_bytes: int = 4, stream=None) -> float:
+    """Relaxations per clock per SM the inner-loop instruction pair sustains on this GPU."""
+    out = ctypes.c_double()
+    _check(load().apsp_measure_peak(dtype_bytes, ctypes.byref(out), _stream_ptr(stream)), "apsp_measure_peak")
+    return out.value
 
 
 PHASES = ("path_init", "phase1_diag", "phase2_panels", "phase3_minplus")

@@ -7,15 +7,24 @@
 // CTA ever waits on another.
 //
 // Per graph (n_g <= 1024, row-major, ld = n_g) the CTA runs the blocked FW of
-// §2.2 with TB = 128 on the matrix in global memory (it stays in L2):
+// §2.2 with TB = 64 on the matrix in global memory (it stays in L2):
 //   phase 1     register-resident closure of the diagonal block (Algorithm 1
 //               restricted to the block, k sequential);
 //   phases 2+3  row block (r,J) <- min(C, D*(r,r) (x) C) and column block
 //               (I,r) <- min(C, C (x) D*(r,r)): once the diagonal block is
 //               closed, the sequential k loop over a panel block equals one
 //               min-plus product with the closed block, so these phases use
-//               the same register-blocked product as phase 4;
+//               the same block product as phase 4;
 //   phase 4     (I,J) <- min(C, D(I,r) (x) D(r,J)).
+// A block product keeps both operand blocks whole in shared memory (all 64
+// values of k, in the k-pair layout of the paired FADD2 + FMNMX3 inner loop).
+// Small graphs run few rounds, so a large share of outputs improves in each;
+// the path matrix is therefore produced in one of two ways, chosen per size
+// class by the autotuner:
+//   variant 0 (lazy):  after the product, improved outputs find their first
+//                      argmin k from the operands still in shared memory;
+//   variant 1 (eager): the inner loop also keeps the argmin k of every
+//                      output (three more instructions per k-pair).
 // On integer-valued weights all sums are exact and D equals every other
 // correct FW; on real weights the phase-2/3 products round differently from
 // the sequential loop (one sum through the closed block instead of a chain of
@@ -34,11 +43,6 @@ namespace apsp {
 
 constexpr int kBatchedMaxN = 1024;
 
-// Size classes and their kernel variants (chosen by the autotuner, see
-// apsp_batched_set_variant).  A variant fixes the block edge and register
-// tile used for the class's graphs inside the one launch:
-//   variant 0: TB = 128, 8 x 8 outputs per thread
-//   variant 1: TB = 64,  4 x 4 outputs per thread (less padding for small n)
 constexpr int kNumClasses = 4;
 static const int32_t kClassLo[kNumClasses] = {1, 65, 129, 257};
 static const int32_t kClassHi[kNumClasses] = {64, 128, 256, kBatchedMaxN};
@@ -46,46 +50,209 @@ __host__ __device__ constexpr int class_of_n(int32_t n) {
   return n <= 64 ? 0 : n <= 128 ? 1 : n <= 256 ? 2 : 3;
 }
 constexpr int kNumVariants = 2;
-static int g_variant[kNumClasses] = {1, 0, 0, 0};
+static int g_variant[kNumClasses] = {1, 1, 0, 0};
 
 static int class_of(int32_t n) { return class_of_n(n); }
 
+namespace b64 {
+constexpr int T = 64;           // block edge
+constexpr int TM = 4;           // 4 x 4 outputs per thread, 256 threads
+constexpr int KP = T / 2;       // k-pairs per block
+constexpr int ST = T + 2;       // row stride of the pair arrays (16-byte rows, fewer conflicts)
+
+struct ProdSmem {
+  unsigned long long As[KP][ST];  // As[kp][i] = (A[i][2kp], A[i][2kp+1])
+  unsigned long long Bs[KP][ST];  // Bs[kp][j] = (B[2kp][j], B[2kp+1][j])
+  float Cs[T][T];                 // new candidates
+  int Ks[T][T];                   // eager variant: first argmin k
+};
+}  // namespace b64
+
 union BatchedSmem {
-  mp32::SmemT<128> prod128;
-  mp32::SmemT<64> prod64;
-  mp32::DiagSmemT<128> diag128;
-  mp32::DiagSmemT<64> diag64;
+  b64::ProdSmem prod;
+  mp32::DiagSmemT<64> diag;
 };
 
-template <int TM>
+__device__ __forceinline__ void relax2_argmin(float &acc, int &idx, unsigned long long a,
+                                              unsigned long long b, int k0) {
+  float c0, c1, m;
+  asm("{\n\t.reg .b64 t;\n\t"
+      "add.rn.f32x2 t, %3, %4;\n\t"
+      "mov.b64 {%0, %1}, t;\n\t"
+      "min.f32 %2, %5, %0, %1;\n\t}"
+      : "=f"(c0), "=f"(c1), "=f"(m)
+      : "l"(a), "l"(b), "f"(acc));
+  (void)c1;
+  if (m < acc) {
+    idx = (c0 == m) ? k0 : k0 + 1;  // the lower k wins a tie inside the pair
+    acc = m;
+  }
+}
+
+// C(baseI, baseJ) <- min(C, A(baseI, baseK) (x) B(baseK, baseJ)), TB = 64,
+// all 256 threads.  C may be the same block as A or B: the operands are
+// copied to shared memory first and C is written only after every read.
+template <bool EAGER>
+__device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t *__restrict__ P,
+                                          int baseI, int baseJ, int baseK, int mI, int mJ, int mK,
+                                          b64::ProdSmem &sm) {
+  using namespace b64;
+  using mp32::col_at;
+  using mp32::row_at;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int ty = mp32::thread_ty(), tx = mp32::thread_tx();
+  const float INF = inf<float>();
+  __syncthreads();  // the previous user of sm is done with it
+  {  // both operand blocks, every element one 4-byte asynchronous copy
+    float *as = reinterpret_cast<float *>(&sm.As[0][0]);
+    float *bs = reinterpret_cast<float *>(&sm.Bs[0][0]);
+#pragma unroll
+    for (int q = 0; q < T * T / 256; ++q) {
+      const int idx = tid + q * 256, i = idx / T, k = idx % T;
+      float *dst = as + ((k >> 1) * ST + i) * 2 + (k & 1);
+      if (i < mI && k < mK) mp32::cp_async4(dst, D + (int64_t)(baseI + i) * ld + baseK + k);
+      else *dst = INF;
+    }
+#pragma unroll
+    for (int q = 0; q < T * T / 256; ++q) {
+      const int idx = tid + q * 256, k = idx / T, j = idx % T;
+      float *dst = bs + ((k >> 1) * ST + j) * 2 + (k & 1);
+      if (j < mJ && k < mK) mp32::cp_async4(dst, D + (int64_t)(baseK + k) * ld + baseJ + j);
+      else *dst = INF;
+    }
+    mp32::cp_async_commit();
+    mp32::cp_async_wait<0>();
+  }
+  __syncthreads();
+  float acc[TM][TM];
+  int kid[TM][TM];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int c = 0; c < TM; ++c) {
+      acc[a][c] = INF;
+      kid[a][c] = -1;
+    }
+  const int kpn = (mK + 1) / 2;
+#pragma unroll 2
+  for (int kp = 0; kp < kpn; ++kp) {
+    unsigned long long a[TM], b[TM];
+#pragma unroll
+    for (int rr = 0; rr < TM; rr += 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[kp][row_at(rr, ty)]);
+      a[rr] = t.x;
+      a[rr + 1] = t.y;
+    }
+#pragma unroll
+    for (int cc = 0; cc < TM; cc += 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.Bs[kp][col_at(cc, tx)]);
+      b[cc] = t.x;
+      b[cc + 1] = t.y;
+    }
+#pragma unroll
+    for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < TM; ++cc) {
+        if (EAGER) relax2_argmin(acc[rr][cc], kid[rr][cc], a[rr], b[cc], 2 * kp);
+        else mp32::relax2(acc[rr][cc], a[rr], b[cc]);
+      }
+  }
+  // Epilogue: candidates (and eager argmins) to shared memory; each warp
+  // then owns 8 whole rows, lane l the columns 2l and 2l+1.
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < TM; cc += 2) {
+      *reinterpret_cast<float2 *>(&sm.Cs[row_at(rr, ty)][col_at(cc, tx)]) =
+          make_float2(acc[rr][cc], acc[rr][cc + 1]);
+      if (EAGER)
+        *reinterpret_cast<int2 *>(&sm.Ks[row_at(rr, ty)][col_at(cc, tx)]) =
+            make_int2(kid[rr][cc], kid[rr][cc + 1]);
+    }
+  __syncthreads();
+  const int i0 = w * 8, j0 = 2 * lane;
+  float o[8][2];
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      o[t][q] = (i0 + t < mI && j0 + q < mJ) ? D[(int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q] : INF;
+  unsigned flags = 0u;  // bit 2t + q: row i0 + t, column j0 + q improved
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (sm.Cs[i0 + t][j0 + q] < o[t][q]) flags |= 1u << (2 * t + q);
+  if (P && !EAGER) {
+    // lazy P: one improved output per warp pass; lane l tests k = 2l, 2l+1
+    // with one paired add of As[l][i] and Bs[l][j] (shared memory).
+    unsigned wflags = __reduce_or_sync(kFullMask, flags);
+#pragma unroll 1
+    while (wflags) {
+      const int t = (__ffs(wflags) - 1) >> 1;
+      wflags &= ~(3u << (2 * t));
+      const int i = i0 + t;
+      unsigned imp = (flags >> (2 * t)) & 3u;
+      unsigned bal = __ballot_sync(kFullMask, imp != 0);
+      const unsigned long long av = sm.As[lane][i];
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        const unsigned sim = __shfl_sync(kFullMask, imp, src);
+        const int q0 = __ffs(sim) - 1;
+        if (lane == src) imp &= imp - 1;
+        if (!(sim & (sim - 1))) bal &= bal - 1;
+        const int sj = 2 * src + q0;
+        const float tgt = sm.Cs[i][sj];
+        const unsigned long long bv = sm.Bs[lane][sj];
+        float c0, c1;
+        asm("{\n\t.reg .b64 t;\n\tadd.rn.f32x2 t, %2, %3;\n\tmov.b64 {%0, %1}, t;\n\t}"
+            : "=f"(c0), "=f"(c1)
+            : "l"(av), "l"(bv));
+        const unsigned h = (c0 == tgt ? 1u : 0u) | (c1 == tgt ? 2u : 0u);
+        const unsigned hb = __ballot_sync(kFullMask, h != 0);
+        const int L = __ffs(hb) - 1;
+        const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
+        if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj] = baseK + 2 * L + (__ffs(hL) - 1);
+      }
+    }
+  }
+  __syncthreads();  // every read of the operands precedes the writes
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if ((flags >> (2 * t + q)) & 1u) {
+        const int64_t g = (int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q;
+        D[g] = sm.Cs[i0 + t][j0 + q];
+        if (EAGER && P) P[g] = baseK + sm.Ks[i0 + t][j0 + q];
+      }
+}
+
+template <bool EAGER>
 __device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *__restrict__ P,
-                                                int n, BatchedSmem &smu) {
-  constexpr int T = 16 * TM;
-  auto &prod = *reinterpret_cast<mp32::SmemT<T> *>(&smu);
-  auto &diag = *reinterpret_cast<mp32::DiagSmemT<T> *>(&smu);
+                                                int n, BatchedSmem &sm) {
+  constexpr int T = b64::T;
   const int ld = n;
-  const int vec_ok = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
   const int R = (n + T - 1) / T;
   for (int r = 0; r < R; ++r) {
     const int base = r * T, m = min(T, n - base);
     __syncthreads();
-    mp32::diag_closure<TM>(D, ld, P, base, m, diag);
+    mp32::diag_closure<4>(D, ld, P, base, m, sm.diag);
     __syncthreads();
     for (int J = 0; J < R; ++J) {
       if (J == r) continue;
-      mp32::block_product<TM>(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, vec_ok, prod);
+      product64<EAGER>(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, sm.prod);
     }
     for (int I = 0; I < R; ++I) {
       if (I == r) continue;
-      mp32::block_product<TM>(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, vec_ok, prod);
+      product64<EAGER>(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, sm.prod);
     }
     __syncthreads();
     for (int I = 0; I < R; ++I) {
       if (I == r) continue;
       for (int J = 0; J < R; ++J) {
         if (J == r) continue;
-        mp32::block_product<TM>(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m,
-                                vec_ok, prod);
+        product64<EAGER>(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m, sm.prod);
       }
     }
   }
@@ -93,7 +260,7 @@ __device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *
 }
 
 // Work item t: graph order[t] & 0x3fffffff, variant order[t] >> 30.
-__global__ void __launch_bounds__(mp32::THREADS, 2)
+__global__ void __launch_bounds__(mp32::THREADS, 3)
     fw_batched_persistent_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
                               const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
                               const int64_t *__restrict__ offs, int num, int *__restrict__ counter) {
@@ -116,9 +283,9 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
       for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[e] = -1;
     }
     if (variant == 1)
-      solve_graph_f32<4>(D, P, n, sm);
+      solve_graph_f32<true>(D, P, n, sm);
     else
-      solve_graph_f32<8>(D, P, n, sm);
+      solve_graph_f32<false>(D, P, n, sm);
   }
 }
 

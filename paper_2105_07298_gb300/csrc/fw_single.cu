@@ -337,33 +337,56 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
     }
   }
   if (!P) return;
-  // Pass 2 (rolled): P for each improved output, one per warp pass; lane l
-  // tests k = 4l..4l+3 of the round (A row and B column, contiguous copies).
-  unsigned long long wflags = __reduce_or_sync(kFullMask, (unsigned)(flags >> 32)) ;
-  wflags = (wflags << 32) | __reduce_or_sync(kFullMask, (unsigned)flags);
+  // Pass 2: P for every improved output.  The warp walks its improved outputs
+  // (all rows, all lanes) as one stream, four at a time: the A-row and B-row
+  // loads of the four are issued together (one memory round trip per group),
+  // then for each output lane l tests k = 4l..4l+3 and the lowest hit wins.
+  unsigned long long wf = __reduce_or_sync(kFullMask, (unsigned)(flags >> 32));
+  wf = (wf << 32) | __reduce_or_sync(kFullMask, (unsigned)flags);
+  unsigned bal = 0u;
+  int pos = 0;
+  auto next = [&](int &t, int &sj) -> bool {  // warp-uniform
+    while (!bal) {
+      if (!wf) return false;
+      pos = __ffsll((long long)wf) - 1;
+      wf &= wf - 1;
+      bal = __ballot_sync(kFullMask, (flags >> pos) & 1ull);
+    }
+    const int src = __ffs(bal) - 1;
+    bal &= bal - 1;
+    t = pos >> 2;
+    sj = 4 * src + (pos & 3);
+    return true;
+  };
 #pragma unroll 1
-  while (wflags) {
-    const int t = (__ffsll((long long)wflags) - 1) >> 2;
-    wflags &= ~(0xfull << (4 * t));
-    const int i = i0 + t;
-    unsigned imp = (unsigned)(flags >> (4 * t)) & 0xfu;
-    unsigned bal = __ballot_sync(kFullMask, imp != 0);
-    const float4 av = reinterpret_cast<const float4 *>(acp + i * T)[lane];
-    while (bal) {
-      const int src = __ffs(bal) - 1;
-      const unsigned sim = __shfl_sync(kFullMask, imp, src);
-      const int q = __ffs(sim) - 1;
-      if (lane == src) imp &= imp - 1;
-      if (!(sim & (sim - 1))) bal &= bal - 1;  // src has no further improved output
-      const int sj = 4 * src + q;
-      const float tgt = Cs[i * T + sj];
-      const float4 bv = reinterpret_cast<const float4 *>(bt + sj * T)[lane];
-      const unsigned h = (__fadd_rn(av.x, bv.x) == tgt ? 1u : 0u) | (__fadd_rn(av.y, bv.y) == tgt ? 2u : 0u) |
-                         (__fadd_rn(av.z, bv.z) == tgt ? 4u : 0u) | (__fadd_rn(av.w, bv.w) == tgt ? 8u : 0u);
+  for (;;) {
+    int t[4], sj[4];
+    bool v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = next(t[u], sj[u]);
+    if (!v[0]) break;
+    float4 av[4], bv[4];
+    float tg[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!v[u]) continue;
+      av[u] = reinterpret_cast<const float4 *>(acp + (i0 + t[u]) * T)[lane];
+      bv[u] = reinterpret_cast<const float4 *>(bt + sj[u] * T)[lane];
+      tg[u] = Cs[(i0 + t[u]) * T + sj[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!v[u]) continue;
+      const float g = tg[u];
+      const unsigned h = (__fadd_rn(av[u].x, bv[u].x) == g ? 1u : 0u) |
+                         (__fadd_rn(av[u].y, bv[u].y) == g ? 2u : 0u) |
+                         (__fadd_rn(av[u].z, bv[u].z) == g ? 4u : 0u) |
+                         (__fadd_rn(av[u].w, bv[u].w) == g ? 8u : 0u);
       const unsigned hb = __ballot_sync(kFullMask, h != 0);
-      const int L = __ffs(hb) - 1;  // hb != 0: tgt is one of the candidates
+      const int L = __ffs(hb) - 1;  // hb != 0: g is one of the candidates
       const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
-      if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj] = baseK + 4 * L + (__ffs(hL) - 1);
+      if (lane == 0 && hb)
+        P[(int64_t)(baseI + i0 + t[u]) * ld + baseJ + sj[u]] = baseK + 4 * L + (__ffs(hL) - 1);
     }
   }
 }

@@ -1,0 +1,104 @@
+// Measured ceiling of the min-plus relaxation on this GPU (a measurement
+// hook; the paper quotes datasheet peaks only, Table 1).
+//
+// The kernel runs the exact instruction pair of the FP32 inner loops - one
+// packed add.rn.f32x2 forming two candidates and one three-input min.f32
+// folding them into an accumulator - on 16 independent accumulators per
+// thread, with no memory traffic, and times itself with the SM clock.  The
+// FP64 variant runs the interval pair (add.rm + add.rp, two mins) that the
+// FP64 path uses per pair of relaxations.
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace apsp {
+
+template <int MODE>
+__global__ void __launch_bounds__(256) peak_kernel(float *out, unsigned long long *cycles, int iters) {
+  constexpr int CH = 16;
+  float acc[CH], acc2[CH];
+  unsigned long long a[CH];
+  const unsigned long long b = 0x3f8000003f800000ull;  // (1.0f, 1.0f)
+#pragma unroll
+  for (int j = 0; j < CH; ++j) {
+    acc[j] = 1e30f;
+    acc2[j] = 1e30f;
+    a[j] = ((unsigned long long)__float_as_uint((float)(threadIdx.x + 2 * j + 1)) << 32) |
+           __float_as_uint((float)(threadIdx.x + 2 * j));
+  }
+  __syncthreads();
+  const unsigned long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      if (MODE == 0) {
+        asm volatile(
+            "{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
+            "add.rn.f32x2 t, %1, %2;\n\tmov.b64 {lo, hi}, t;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
+            : "+f"(acc[j])
+            : "l"(a[j]), "l"(b));
+      } else {  // lower and upper bound of the same two candidates
+        asm volatile(
+            "{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
+            "add.rm.f32x2 t, %1, %2;\n\tmov.b64 {lo, hi}, t;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
+            : "+f"(acc[j])
+            : "l"(a[j]), "l"(b));
+        asm volatile(
+            "{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
+            "add.rp.f32x2 t, %1, %2;\n\tmov.b64 {lo, hi}, t;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
+            : "+f"(acc2[j])
+            : "l"(a[j]), "l"(b));
+      }
+    }
+  }
+  const unsigned long long t1 = clock64();
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < CH; ++j) s += acc[j] + acc2[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace apsp
+
+// Runs the relaxation loop (dtype_bytes 4: FP32 pair; 8: FP64 interval pair)
+// on every SM and writes the achieved relaxations per clock per SM.  Uses the
+// caller's stream; synchronises it.  Scratch comes from stream-ordered
+// allocation and is freed before returning.
+APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm, void *stream) {
+  if (!relax_per_clk_per_sm || (dtype_bytes != 4 && dtype_bytes != 8)) return APSP_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int blocks = sms * 4, threads = 256, iters = 4096;
+  float *out = nullptr;
+  unsigned long long *cyc = nullptr;
+  cudaGetLastError();
+  if (cudaMallocAsync((void **)&out, (size_t)blocks * threads * 4, s) != cudaSuccess) return APSP_ENOMEM;
+  if (cudaMallocAsync((void **)&cyc, (size_t)blocks * 8, s) != cudaSuccess) {
+    cudaFreeAsync(out, s);
+    return APSP_ENOMEM;
+  }
+  for (int rep = 0; rep < 2; ++rep) {  // the first pass warms clocks and caches
+    if (dtype_bytes == 4) apsp::peak_kernel<0><<<blocks, threads, 0, s>>>(out, cyc, iters);
+    else apsp::peak_kernel<1><<<blocks, threads, 0, s>>>(out, cyc, iters);
+  }
+  unsigned long long *h = new unsigned long long[blocks];
+  cudaError_t e = cudaMemcpyAsync(h, cyc, (size_t)blocks * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(out, s);
+  cudaFreeAsync(cyc, s);
+  if (e != cudaSuccess) {
+    delete[] h;
+    return APSP_ECUDA;
+  }
+  unsigned long long mx = 1;
+  for (int i = 0; i < blocks; ++i) mx = h[i] > mx ? h[i] : mx;
+  delete[] h;
+  // all blocks are resident at once (4 x 256 threads per SM); relaxations per
+  // pair-instruction: 2 (FP32) or 2 FP64 relaxations per interval pair.
+  const double relax = 2.0 * 16.0 * iters * (double)threads * blocks;
+  *relax_per_clk_per_sm = relax / sms / (double)mx;
+  return APSP_OK;
+}
