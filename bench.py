@@ -144,7 +144,9 @@ class ClockSampler:
                     reasons.add(name)
         loaded = [r for r in rows if r[2] > 200.0] or rows
         return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
-                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+                "power_w_max": max(r[2] for r in rows),
+                "power_w_mean": statistics.mean(r[2] for r in loaded),
+                "samples": len(rows), "reasons": sorted(reasons)}
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -530,6 +532,12 @@ def run_ours(args):
         "phase_time_ms": phase_share,
         "gpu_launches": launches,
         "clocks": clocks,
+        # the paper's Table 3 metric: Eq. 1 GFLOPS (2 per relaxation) per watt of
+        # board power sampled during the timed region
+        "energy": ({"power_w_mean": clocks["power_w_mean"],
+                    "eq1_gflops_per_w": 2 * value / world / 1e9 / clocks["power_w_mean"],
+                    "relax_per_joule": value / world / clocks["power_w_mean"]}
+                   if clocks and clocks.get("power_w_mean") else None),
         "device": facts,
     }
 

@@ -41,19 +41,22 @@ namespace apsp {
 namespace f64 {
 
 constexpr int T = 128;
-constexpr int THREADS = 512;  // product: 16 warps, 4 x 8 outputs per thread
+constexpr int THREADS = 256;  // product: 8 warps, 4 x 8 outputs per thread, 128 x 64 per CTA
+constexpr int H = T / 2;      // output columns per CTA (one half of a block)
 constexpr int KS = 32, KP = 16, STAGES = 2;
-constexpr uint32_t SLAB_BYTES = KP * T * 8;
+constexpr uint32_t SLAB_BYTES = KP * H * 8;  // one half of one paired array, one slab
 
 // One operand block packed for the product kernel.  For an A operand
-// (A[i][k]): lo[kp][i] = (rd A[i][2kp], rd A[i][2kp+1]), hi likewise with ru,
-// rlo[i][k] = rd A[i][k], rhi[i][k] = ru A[i][k], r64[i][k] = A[i][k].
-// For a B operand (B[k][j]): lo[kp][j] = (rd B[2kp][j], rd B[2kp+1][j]), ...,
-// rlo[j][k] = rd B[k][j], rhi[j][k], r64[j][k] = B[k][j] (transposed).
-// Entries outside the matrix hold +inf.
+// (A[i][k]): lo[i/64][kp][i%64] = (rd A[i][2kp], rd A[i][2kp+1]), hi likewise
+// with ru, rlo[i][k] = rd A[i][k], rhi[i][k] = ru A[i][k], r64[i][k] = A[i][k].
+// For a B operand (B[k][j]): lo[j/64][kp][j%64] = (rd B[2kp][j],
+// rd B[2kp+1][j]), ..., rlo[j][k] = rd B[k][j], rhi[j][k], r64[j][k] = B[k][j]
+// (transposed).  The paired arrays are split in two 64-wide halves so that a
+// 16-k-pair slab of one half is one contiguous 8 KiB piece.  Entries outside
+// the matrix hold +inf.
 struct Pack {
-  unsigned long long lo[T / 2][T];
-  unsigned long long hi[T / 2][T];
+  unsigned long long lo[2][T / 2][T / 2];
+  unsigned long long hi[2][T / 2][T / 2];
   float rlo[T][T];
   float rhi[T][T];
   double r64[T][T];
@@ -133,8 +136,8 @@ __device__ void pack_block(const double *s, Pack *pk, bool as_b) {
     const int kp = e / T, x = e % T;
     const double v0 = as_b ? s[(2 * kp) * S + x] : s[x * S + 2 * kp];
     const double v1 = as_b ? s[(2 * kp + 1) * S + x] : s[x * S + 2 * kp + 1];
-    pk->lo[kp][x] = packf2(f64_down(v0), f64_down(v1));
-    pk->hi[kp][x] = packf2(f64_up(v0), f64_up(v1));
+    pk->lo[x >> 6][kp][x & 63] = packf2(f64_down(v0), f64_down(v1));
+    pk->hi[x >> 6][kp][x & 63] = packf2(f64_up(v0), f64_up(v1));
   }
   for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
     const int x = e / T, k = e % T;  // row x of the row-contiguous copies
@@ -245,67 +248,72 @@ __global__ void __launch_bounds__(K2A_THREADS)
 }
 
 // ---------------------------------------------------------------- products
-// MODE 0: phase 4, C = (I,J), A = packA[I], B = packB[J] (grid (R-1)^2)
-// MODE 1: phase 2, C = (r,J), A = diagA,    B = packB[J] (grid R-1), re-packs C into packB[J]
-// MODE 2: phase 3, C = (I,r), A = packA[I], B = diagB    (grid R-1), re-packs C into packA[I]
+// A CTA computes one 128 x 64 half of an output block (two CTAs per block, two
+// CTAs per SM):
+// MODE 0: phase 4, C = (I,J), A = packA[I], B = packB[J] (grid 2 (R-1)^2)
+// MODE 1: phase 2, C = (r,J), A = diagA,    B = packB[J] (grid 2 (R-1)), re-packs C into packB[J]
+// MODE 2: phase 3, C = (I,r), A = packA[I], B = diagB    (grid 2 (R-1)), re-packs C into packA[I]
 struct ProdSmem {
-  unsigned long long Alo[STAGES][KP][T];
-  unsigned long long Ahi[STAGES][KP][T];
-  unsigned long long Blo[STAGES][KP][T];
-  unsigned long long Bhi[STAGES][KP][T];
+  unsigned long long Alo[STAGES][2][KP][H];  // both row halves of the A slab
+  unsigned long long Ahi[STAGES][2][KP][H];
+  unsigned long long Blo[STAGES][KP][H];     // this CTA's column half of the B slab
+  unsigned long long Bhi[STAGES][KP][H];
   uint64_t bar[STAGES];
 };
 
-// Thread (warp w, lane l): wy = w/2 (0..7), wx = w%2, ly = l/8, lx = l%8;
-//   rows i(r) = (r>>1)*64 + wy*8 + ly*2 + (r&1)            (r = 0..3)
-//   cols j(c) = (c>>2)*64 + wx*32 + ((c>>1)&1)*16 + lx*2 + (c&1)   (c = 0..7)
-__device__ __forceinline__ int row4(int r, int wy, int ly) {
-  return (r >> 1) * 64 + wy * 8 + ly * 2 + (r & 1);
-}
-__device__ __forceinline__ int col8(int c, int wx, int lx) {
-  return (c >> 2) * 64 + wx * 32 + ((c >> 1) & 1) * 16 + lx * 2 + (c & 1);
-}
+// Thread (warp w, lane l): ty = 4w + l/8 (0..31), tx = l%8 (0..7);
+//   rows i(r) = (r>>1)*64 + ty*2 + (r&1)        (r = 0..3, row half r>>1)
+//   cols j(c) = (c>>1)*16 + tx*2 + (c&1)        (c = 0..7, within the CTA's half)
+// Row and column pairs are adjacent, so each pair is one 16-byte shared load;
+// a warp's loads of one k-pair touch 64 (A) and 128 (B) consecutive bytes.
+__device__ __forceinline__ int row4(int r, int ty) { return (r >> 1) * 64 + ty * 2 + (r & 1); }
+__device__ __forceinline__ int col8(int c, int tx) { return (c >> 1) * 16 + tx * 2 + (c & 1); }
 
-__device__ __forceinline__ void issue_slab(ProdSmem &sm, int st, const Pack *A, const Pack *B, int s) {
-  mbar_expect_tx(&sm.bar[st], 4 * SLAB_BYTES);
-  bulk_g2s(&sm.Alo[st][0][0], &A->lo[s * KP][0], SLAB_BYTES, &sm.bar[st]);
-  bulk_g2s(&sm.Ahi[st][0][0], &A->hi[s * KP][0], SLAB_BYTES, &sm.bar[st]);
-  bulk_g2s(&sm.Blo[st][0][0], &B->lo[s * KP][0], SLAB_BYTES, &sm.bar[st]);
-  bulk_g2s(&sm.Bhi[st][0][0], &B->hi[s * KP][0], SLAB_BYTES, &sm.bar[st]);
+__device__ __forceinline__ void issue_slab(ProdSmem &sm, int st, const Pack *A, const Pack *B, int hJ,
+                                           int s) {
+  mbar_expect_tx(&sm.bar[st], 6 * SLAB_BYTES);
+  for (int h = 0; h < 2; ++h) {
+    bulk_g2s(&sm.Alo[st][h][0][0], &A->lo[h][s * KP][0], SLAB_BYTES, &sm.bar[st]);
+    bulk_g2s(&sm.Ahi[st][h][0][0], &A->hi[h][s * KP][0], SLAB_BYTES, &sm.bar[st]);
+  }
+  bulk_g2s(&sm.Blo[st][0][0], &B->lo[hJ][s * KP][0], SLAB_BYTES, &sm.bar[st]);
+  bulk_g2s(&sm.Bhi[st][0][0], &B->hi[hJ][s * KP][0], SLAB_BYTES, &sm.bar[st]);
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
     fw64_product(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R,
                  Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   ProdSmem &sm = *reinterpret_cast<ProdSmem *>(smem_raw);
+  const int tile = blockIdx.x >> 1, hJ = blockIdx.x & 1;
   int I, J;
   if (MODE == 0) {
-    I = blockIdx.x / (R - 1);
-    J = blockIdx.x % (R - 1);
+    I = tile / (R - 1);
+    J = tile % (R - 1);
     I += (I >= r);
     J += (J >= r);
   } else if (MODE == 1) {
     I = r;
-    J = blockIdx.x + (blockIdx.x >= r);
+    J = tile + (tile >= r);
   } else {
-    I = blockIdx.x + (blockIdx.x >= r);
+    I = tile + (tile >= r);
     J = r;
   }
   const Pack *A = MODE == 1 ? diagA : &packA[I];
   const Pack *B = MODE == 2 ? diagB : &packB[J];
-  const int baseI = I * T, baseJ = J * T, baseK = r * T;
-  const int mI = min(T, n - baseI), mJ = min(T, n - baseJ), mK = min(T, n - baseK);
+  const int baseI = I * T, baseJ = J * T + hJ * H, baseK = r * T;
+  const int mI = min(T, n - baseI), mJ = min(H, n - baseJ), mK = min(T, n - baseK);
+  if (mJ <= 0) return;  // an empty half: its packs already hold +inf (uniform exit, no barrier used)
   const int nslab = (mK + KS - 1) / KS;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int wy = w >> 1, wx = w & 1, ly = lane >> 3, lx = lane & 7;
+  const int ty = 4 * w + (lane >> 3), tx = lane & 7;
   const float FINF = __int_as_float(0x7f800000);
 
   if (tid == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(&sm.bar[st], 1);
     fence_mbar_init();
-    for (int s = 0; s < STAGES && s < nslab; ++s) issue_slab(sm, s, A, B, s);
+    for (int s = 0; s < STAGES && s < nslab; ++s) issue_slab(sm, s, A, B, hJ, s);
   }
   __syncthreads();
 
@@ -330,17 +338,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     // its lo products run, and the lo operands of kp+1 while its hi products
     // run (two named operand sets; the compiler's unrolling would spill).
     unsigned long long al[4], bl[8], ah[4], bh[8];
-    auto load_set = [&](int kp, const unsigned long long (*As)[T], const unsigned long long (*Bs)[T],
+    auto load_set = [&](int kp, const unsigned long long (*As)[KP][H], const unsigned long long (*Bs)[H],
                         unsigned long long (&a)[4], unsigned long long (&b)[8]) {
 #pragma unroll
       for (int rr = 0; rr < 4; rr += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&As[kp][row4(rr, wy, ly)]);
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&As[rr >> 1][kp][ty * 2]);
         a[rr] = t.x;
         a[rr + 1] = t.y;
       }
 #pragma unroll
       for (int cc = 0; cc < 8; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bs[kp][col8(cc, wx, lx)]);
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bs[kp][col8(cc, tx)]);
         b[cc] = t.x;
         b[cc + 1] = t.y;
       }
@@ -362,74 +370,112 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     if (tid == 0 && s + STAGES < nslab) {
       fence_proxy_async_smem();
-      issue_slab(sm, st, A, B, s + STAGES);
+      issue_slab(sm, st, A, B, hJ, s + STAGES);
     }
   }
 
   // Epilogue.  The ring is free: min-lo and min-up go to shared memory, then
-  // each warp owns 8 whole rows (lane l: columns 4l..4l+3) in compact rolled
-  // loops (small code, coalesced global accesses).  Per output:
+  // each warp owns 16 whole rows (lane l: columns 2l, 2l+1 of the half).
+  // Per output:
   //   X = min lo >= ru(old):          nothing can beat old;
   //   X == min up (exact min = X):    improved iff X < old; P recovered below;
   //   otherwise ("slow"):             exact FP64 resolution below.
   // D may be written at once: the recovery reads only the packed operands.
-  float *Lo = reinterpret_cast<float *>(smem_raw);  // [T][T]
-  float *Up = Lo + T * T;                           // [T][T]
+  float *Lo = reinterpret_cast<float *>(smem_raw);  // [T][H]
+  float *Up = Lo + T * H;                           // [T][H]
   __syncthreads();
 #pragma unroll
   for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
     for (int cc = 0; cc < 8; cc += 2) {
-      const int i = row4(rr, wy, ly), j = col8(cc, wx, lx);
-      *reinterpret_cast<float2 *>(&Lo[i * T + j]) = make_float2(lo[rr][cc], lo[rr][cc + 1]);
-      *reinterpret_cast<float2 *>(&Up[i * T + j]) = make_float2(up[rr][cc], up[rr][cc + 1]);
+      const int i = row4(rr, ty), j = col8(cc, tx);
+      *reinterpret_cast<float2 *>(&Lo[i * H + j]) = make_float2(lo[rr][cc], lo[rr][cc + 1]);
+      *reinterpret_cast<float2 *>(&Up[i * H + j]) = make_float2(up[rr][cc], up[rr][cc + 1]);
     }
   __syncthreads();
-  const int j0 = 4 * lane;
-#pragma unroll 1
-  for (int i = w * 8; i < w * 8 + 8; ++i) {
-    if (i >= mI) break;
-    double *row = D + (int64_t)(baseI + i) * ld + baseJ;
-    unsigned quick = 0u, slow = 0u;
+  const int j0 = 2 * lane, i0 = w * 16;
+  // Pass 1 (unrolled): the warp's 16 x 64 old values are loaded before any is
+  // used (one memory round trip); outputs are classified and quick
+  // improvements written.  Bit 2t + q of quick/slow: row i0 + t, column j0 + q.
+  double o[16][2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = j0 + q;
-      if (j >= mJ) continue;
-      const double old = row[j];
-      const float X = Lo[i * T + j];
-      if (!(X < f64_up(old))) continue;
-      if (X == Up[i * T + j]) {
+  for (int t = 0; t < 16; ++t)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      o[t][q] = (i0 + t < mI && j0 + q < mJ) ? D[(int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q]
+                                             : inf<double>();
+  unsigned quick = 0u, slow = 0u;
+#pragma unroll
+  for (int t = 0; t < 16; ++t)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = i0 + t, j = j0 + q;
+      if (i >= mI || j >= mJ) continue;
+      const float X = Lo[i * H + j];
+      if (!(X < f64_up(o[t][q]))) continue;
+      if (X == Up[i * H + j]) {
         const unsigned long long xb = f32_to_f64_bits(X);
-        if (dkey(xb) < dkey((unsigned long long)__double_as_longlong(old))) {
-          row[j] = __longlong_as_double((long long)xb);
-          quick |= 1u << q;
+        if (dkey(xb) < dkey((unsigned long long)__double_as_longlong(o[t][q]))) {
+          D[(int64_t)(baseI + i) * ld + baseJ + j] = __longlong_as_double((long long)xb);
+          quick |= 1u << (2 * t + q);
         }
       } else {
-        slow |= 1u << q;
+        slow |= 1u << (2 * t + q);
       }
     }
-    unsigned todo = quick | slow;
-    unsigned bal = __ballot_sync(kFullMask, todo != 0);
-    if (!bal) continue;
-    const float4 alo = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
-    const float4 ahi = reinterpret_cast<const float4 *>(&A->rhi[i][0])[lane];
-    const float la[4] = {alo.x, alo.y, alo.z, alo.w}, ha[4] = {ahi.x, ahi.y, ahi.z, ahi.w};
-    while (bal) {
-      const int src = __ffs(bal) - 1;
-      const unsigned stodo = __shfl_sync(kFullMask, todo, src);
-      const unsigned sslow = __shfl_sync(kFullMask, slow, src);
-      const int q0 = __ffs(stodo) - 1;
-      if (lane == src) todo &= todo - 1;
-      if (!(stodo & (stodo - 1))) bal &= bal - 1;
-      const bool is_slow = (sslow >> q0) & 1u;
-      const int sj = 4 * src + q0;
-      const int64_t g = (int64_t)(baseI + i) * ld + baseJ + sj;
-      const float X = Lo[i * T + sj];
-      const double old = D[g];  // quick: already the new value (unused)
-      const float th = is_slow ? fminf(Up[i * T + sj], f64_up(old)) : X;
-      const float4 blo = reinterpret_cast<const float4 *>(&B->rlo[sj][0])[lane];
-      const float4 bhi = reinterpret_cast<const float4 *>(&B->rhi[sj][0])[lane];
-      const float lb[4] = {blo.x, blo.y, blo.z, blo.w}, hb[4] = {bhi.x, bhi.y, bhi.z, bhi.w};
+  // Pass 2: every flagged output, the warp's flagged outputs walked as one
+  // stream two at a time (the bound rows of both load together); lane l
+  // tests k = 4l..4l+3.  quick: recover the first k whose exact sum is X;
+  // slow: exact FP64 minimum over the candidates with lo <= min(up, ru(old)).
+  const unsigned todo = quick | slow;
+  unsigned wf = __reduce_or_sync(kFullMask, todo);
+  unsigned bal = 0u;
+  int pos = 0;
+  auto next = [&](int &t, int &sj, bool &is_slow) -> bool {  // warp-uniform
+    while (!bal) {
+      if (!wf) return false;
+      pos = __ffs(wf) - 1;
+      wf &= wf - 1;
+      bal = __ballot_sync(kFullMask, (todo >> pos) & 1u);
+    }
+    const int src = __ffs(bal) - 1;
+    bal &= bal - 1;
+    t = pos >> 1;
+    sj = 2 * src + (pos & 1);
+    is_slow = (__shfl_sync(kFullMask, slow, src) >> pos) & 1u;
+    return true;
+  };
+  const int jb0 = hJ * H;  // column offset of this half inside the B pack
+#pragma unroll 1
+  for (;;) {
+    int t[2], sj[2];
+    bool sl[2], v[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) v[u] = next(t[u], sj[u], sl[u]);
+    if (!v[0]) break;
+    float4 alo[2], ahi[2], blo[2], bhi[2];
+    double old[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!v[u]) continue;
+      const int i = i0 + t[u];
+      alo[u] = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
+      ahi[u] = reinterpret_cast<const float4 *>(&A->rhi[i][0])[lane];
+      blo[u] = reinterpret_cast<const float4 *>(&B->rlo[jb0 + sj[u]][0])[lane];
+      bhi[u] = reinterpret_cast<const float4 *>(&B->rhi[jb0 + sj[u]][0])[lane];
+      old[u] = D[(int64_t)(baseI + i) * ld + baseJ + sj[u]];  // quick: already the new value (unused)
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!v[u]) continue;
+      const int i = i0 + t[u];
+      const int64_t g = (int64_t)(baseI + i) * ld + baseJ + sj[u];
+      const float X = Lo[i * H + sj[u]];
+      const float th = sl[u] ? fminf(Up[i * H + sj[u]], f64_up(old[u])) : X;
+      const float la[4] = {alo[u].x, alo[u].y, alo[u].z, alo[u].w};
+      const float ha[4] = {ahi[u].x, ahi[u].y, ahi[u].z, ahi[u].w};
+      const float lb[4] = {blo[u].x, blo[u].y, blo[u].z, blo[u].w};
+      const float hb[4] = {bhi[u].x, bhi[u].y, bhi[u].z, bhi[u].w};
       long long best = 0x7fffffffffffffffll;
       int bestk = 0x7fffffff;
 #pragma unroll
@@ -437,10 +483,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int k = 4 * lane + q;
         const float l = __fadd_rd(la[q], lb[q]);
         if (l <= th) {
-          const float u = __fadd_ru(ha[q], hb[q]);
+          const float up_ = __fadd_ru(ha[q], hb[q]);
           unsigned long long vb;
-          if (l == u) vb = f32_to_f64_bits(l);
-          else vb = (unsigned long long)__double_as_longlong(__dadd_rn(A->r64[i][k], B->r64[sj][k]));
+          if (l == up_) vb = f32_to_f64_bits(l);
+          else vb = (unsigned long long)__double_as_longlong(__dadd_rn(A->r64[i][k], B->r64[jb0 + sj[u]][k]));
           const long long key = dkey(vb);
           if (key < best) {
             best = key;
@@ -458,8 +504,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (lane == 0 && bestk != 0x7fffffff) {
-        if (is_slow) {
-          if (best < dkey((unsigned long long)__double_as_longlong(old))) {
+        if (sl[u]) {
+          if (best < dkey((unsigned long long)__double_as_longlong(old[u]))) {
             D[g] = __longlong_as_double((long long)dkey_bits(best));
             if (P) P[g] = baseK + bestk;
           }
@@ -470,27 +516,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   }
   if (MODE == 0) return;
-  // Phases 2/3: re-pack the updated block for this round's phase 4.
+  // Phases 2/3: re-pack this half of the updated block for the round's phase 4.
   __syncthreads();
   Pack *dst = MODE == 1 ? &packB[J] : &packA[I];
 #pragma unroll
   for (int rr = 0; rr < 4; rr += 2) {
-    const int i0 = row4(rr, wy, ly);  // rows i0, i0 + 1
+    const int i0p = row4(rr, ty);  // rows i0p, i0p + 1 of the block
 #pragma unroll
     for (int cc = 0; cc < 8; cc += 2) {
-      const int j0 = col8(cc, wx, lx);  // cols j0, j0 + 1
+      const int j0l = col8(cc, tx);  // columns j0l, j0l + 1 of the half
+      const int jb = jb0 + j0l;      // ... of the block
       double v[2][2];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int c = 0; c < 2; ++c)
-          v[a][c] = (i0 + a < mI && j0 + c < mJ) ? D[(int64_t)(baseI + i0 + a) * ld + baseJ + j0 + c]
-                                                 : inf<double>();
+          v[a][c] = (i0p + a < mI && j0l + c < mJ)
+                        ? D[(int64_t)(baseI + i0p + a) * ld + baseJ + j0l + c]
+                        : inf<double>();
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const int i = i0 + a, j = j0 + c;
+          const int i = i0p + a, j = jb + c;
           const float vl = f64_down(v[a][c]), vh = f64_up(v[a][c]);
           if (MODE == 1) {  // B operand: [j][k = i]
             dst->rlo[j][i] = vl;
@@ -502,17 +550,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             dst->r64[i][j] = v[a][c];
           }
         }
-      if (MODE == 1) {  // pairs along k = rows i0, i0 + 1
+      if (MODE == 1) {  // pairs along k = rows i0p, i0p + 1; column jb + c of the B pack
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          dst->lo[i0 / 2][j0 + c] = packf2(f64_down(v[0][c]), f64_down(v[1][c]));
-          dst->hi[i0 / 2][j0 + c] = packf2(f64_up(v[0][c]), f64_up(v[1][c]));
+          dst->lo[(jb + c) >> 6][i0p / 2][(jb + c) & 63] = packf2(f64_down(v[0][c]), f64_down(v[1][c]));
+          dst->hi[(jb + c) >> 6][i0p / 2][(jb + c) & 63] = packf2(f64_up(v[0][c]), f64_up(v[1][c]));
         }
-      } else {  // pairs along k = cols j0, j0 + 1
+      } else {  // pairs along k = block columns jb, jb + 1; row i of the A pack
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-          dst->lo[j0 / 2][i0 + a] = packf2(f64_down(v[a][0]), f64_down(v[a][1]));
-          dst->hi[j0 / 2][i0 + a] = packf2(f64_up(v[a][0]), f64_up(v[a][1]));
+          const int i = i0p + a;
+          dst->lo[i >> 6][jb / 2][i & 63] = packf2(f64_down(v[a][0]), f64_down(v[a][1]));
+          dst->hi[i >> 6][jb / 2][i & 63] = packf2(f64_up(v[a][0]), f64_up(v[a][1]));
         }
       }
     }
@@ -555,12 +604,12 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
       {
         PhaseScope ps(2, s);
         fw64_pack_panels<<<2 * (R - 1), K2A_THREADS, smem2a, s>>>(D, ld, n, r, R, packA, packB);
-        fw64_product<1><<<R - 1, THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
-        fw64_product<2><<<R - 1, THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
+        fw64_product<1><<<2 * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
+        fw64_product<2><<<2 * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
       }
       PhaseScope ps(3, s);
-      fw64_product<0><<<(R - 1) * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA,
-                                                                 diagB);
+      fw64_product<0><<<2 * (R - 1) * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB,
+                                                                     diagA, diagB);
     }
   }
   cudaError_t e = cudaGetLastError();

@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
   }
   if (!P) return;
   // Pass 2: P for every improved output.  The warp walks its improved outputs
-  // (all rows, all lanes) as one stream, four at a time: the A-row and B-row
-  // loads of the four are issued together (one memory round trip per group),
+  // (all rows, all lanes) as one stream, eight at a time: the A-row and B-row
+  // loads of the eight are issued together (one memory round trip per group),
   // then for each output lane l tests k = 4l..4l+3 and the lowest hit wins.
   unsigned long long wf = __reduce_or_sync(kFullMask, (unsigned)(flags >> 32));
   wf = (wf << 32) | __reduce_or_sync(kFullMask, (unsigned)flags);
@@ -360,22 +360,22 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
   };
 #pragma unroll 1
   for (;;) {
-    int t[4], sj[4];
-    bool v[4];
+    int t[8], sj[8];
+    bool v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = next(t[u], sj[u]);
+    for (int u = 0; u < 8; ++u) v[u] = next(t[u], sj[u]);
     if (!v[0]) break;
-    float4 av[4], bv[4];
-    float tg[4];
+    float4 av[8], bv[8];
+    float tg[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       if (!v[u]) continue;
       av[u] = reinterpret_cast<const float4 *>(acp + (i0 + t[u]) * T)[lane];
       bv[u] = reinterpret_cast<const float4 *>(bt + sj[u] * T)[lane];
       tg[u] = Cs[(i0 + t[u]) * T + sj[u]];
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       if (!v[u]) continue;
       const float g = tg[u];
       const unsigned h = (__fadd_rn(av[u].x, bv[u].x) == g ? 1u : 0u) |
