@@ -53,7 +53,7 @@ __global__ void fw_path_init(int32_t *__restrict__ P, int64_t n, int64_t ld) {
 //   column block: own[i][j] = min(own[i][j], own[i][k] + diag[k][j])
 // When `pan` is given (FP32), the finished blocks are also written, padded
 // with +inf to full T x T, in the layouts phase 4 reads this round:
-//   row block (r,J):    Bpan[J][kp][j] = (own[2kp][j], own[2kp+1][j]),
+//   row block (r,J):    Bpan[J][j/64][kp][j%64] = (own[2kp][j], own[2kp+1][j]),
 //                       Bt[J][j][k] = own[k][j]
 //   column block (I,r): Apan[I][kp][i] = (own[i][2kp], own[i][2kp+1]),
 //                       Acp[I][i][k] = own[i][k]
@@ -140,7 +140,10 @@ __global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D
         const float hi = is_row ? o[(2 * kp + 1) * S + x] : o[x * S + 2 * kp + 1];
         const unsigned long long v =
             ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-        (is_row ? pan.Bpan : pan.Apan)[(blk * (T / 2) + kp) * T + x] = v;
+        if (is_row)  // two 64-wide halves, so a phase-4 CTA's B slab is contiguous
+          pan.Bpan[((blk * 2 + (x >> 6)) * (T / 2) + kp) * (T / 2) + (x & 63)] = v;
+        else
+          pan.Apan[(blk * (T / 2) + kp) * T + x] = v;
       }
       for (int e = tid; e < T * T; e += THREADS) {
         const int x = e / T, k = e % T;  // Bt[J][j][k] = own[k][j]; Acp[I][i][k] = own[i][k]
@@ -163,24 +166,25 @@ __global__ void __launch_bounds__(mp32::THREADS)
   mp32::diag_closure<8>(D, ld, P, base, min(mp32::T, n - base), sm);
 }
 
-// K3 (FP32) stages its operands with bulk copies from the panel buffers K2
-// wrote (already in the paired shared-memory layout and padded with +inf, so
-// the main loop needs no bounds checks): per 32-k slab one 16 KiB copy of A
-// and one of B into a two-stage ring, completion tracked by an mbarrier per
-// stage.  P recovery reads the row-contiguous copies Acp/Bt (one float4 of
-// each per lane: the 128 candidate sums of an output in one round trip).
+// K3 (FP32): one CTA computes one 128 x 64 half of an output block (two CTAs
+// per block, three CTAs per SM); each thread owns an 8 x 4 register tile.  The
+// operands come from the panel buffers K2 wrote (already in the paired
+// shared-memory layout and padded with +inf, so the main loop needs no bounds
+// checks): per 32-k slab one 16 KiB bulk copy of A and one 8 KiB copy of B
+// into a two-stage ring, completion tracked by an mbarrier per stage.  Path
+// recovery reads the row-contiguous copies Acp/Bt (one float4 of each per
+// lane: the 128 candidate sums of an output in one memory round trip).
 namespace k3 {
-constexpr int T = mp32::T, KS = mp32::KS, KP = mp32::KP, STAGES = 2;
-constexpr uint32_t SLAB_BYTES = KP * T * 8;  // one operand, one slab
+constexpr int T = mp32::T, KS = mp32::KS, KP = mp32::KP, STAGES = 2, H = T / 2;
+constexpr uint32_t A_SLAB = KP * T * 8, B_SLAB = KP * H * 8;
 struct Smem {
-  unsigned long long As[STAGES][KP][T];
-  unsigned long long Bs[STAGES][KP][T];
+  unsigned long long As[STAGES][KP][T];  // As[kp][i] = (A[i][2kp], A[i][2kp+1])
+  unsigned long long Bs[STAGES][KP][H];  // Bs[kp][j] = (B[2kp][j], B[2kp+1][j]), this half
   uint64_t bar[STAGES];
-  int fail;
 };
 }  // namespace k3
 
-__global__ void __launch_bounds__(mp32::THREADS, 2)
+__global__ void __launch_bounds__(mp32::THREADS, 3)
     fw_phase3_minplus_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
                           int R, int vec_ok, Panels pan) {
   using namespace k3;
@@ -188,36 +192,36 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
   using mp32::row_at;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
-  const int Rm = R - 1;
-  int I = blockIdx.x / Rm, J = blockIdx.x % Rm;
+  const int Rm = R - 1, tile = blockIdx.x >> 1, hJ = blockIdx.x & 1;
+  int I = tile / Rm, J = tile % Rm;
   I += (I >= r);
   J += (J >= r);
-  const int baseI = I * T, baseJ = J * T, baseK = r * T;
-  const int mI = min(T, n - baseI), mJ = min(T, n - baseJ), mK = min(T, n - baseK);
+  const int baseI = I * T, baseJ = J * T + hJ * H, baseK = r * T;
+  const int mI = min(T, n - baseI), mJ = min(H, n - baseJ), mK = min(T, n - baseK);
+  if (mJ <= 0) return;  // empty half of the last (narrow) block; uniform exit
   const int nslab = (mK + KS - 1) / KS;
   const int tid = threadIdx.x, lane = tid & 31;
   const int ty = mp32::thread_ty(), tx = mp32::thread_tx();
   const float INF = inf<float>();
   const unsigned long long *srcA = pan.Apan + (int64_t)I * (T / 2) * T;
-  const unsigned long long *srcB = pan.Bpan + (int64_t)J * (T / 2) * T;
+  const unsigned long long *srcB = pan.Bpan + ((int64_t)J * 2 + hJ) * (T / 2) * H;
 
   if (tid == 0) {
-    sm.fail = 0;
     for (int st = 0; st < STAGES; ++st) mbar_init(&sm.bar[st], 1);
     fence_mbar_init();
     for (int s = 0; s < STAGES && s < nslab; ++s) {
-      mbar_expect_tx(&sm.bar[s], 2 * SLAB_BYTES);
-      bulk_g2s(&sm.As[s][0][0], srcA + (int64_t)s * KP * T, SLAB_BYTES, &sm.bar[s]);
-      bulk_g2s(&sm.Bs[s][0][0], srcB + (int64_t)s * KP * T, SLAB_BYTES, &sm.bar[s]);
+      mbar_expect_tx(&sm.bar[s], A_SLAB + B_SLAB);
+      bulk_g2s(&sm.As[s][0][0], srcA + (int64_t)s * KP * T, A_SLAB, &sm.bar[s]);
+      bulk_g2s(&sm.Bs[s][0][0], srcB + (int64_t)s * KP * H, B_SLAB, &sm.bar[s]);
     }
   }
   __syncthreads();
 
-  float acc[8][8];
+  float acc[8][4];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[a][c] = INF;
+    for (int c = 0; c < 4; ++c) acc[a][c] = INF;
 
   for (int s = 0; s < nslab; ++s) {
     const int st = s % STAGES;
@@ -232,34 +236,33 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
       }
       return;
     }
-    // Operand loads are software-pipelined by hand (the compiler's own
-    // unrolling would exceed 128 registers): the B pairs of k-pair kp+1 load
-    // while kp computes (two named buffers, k-pairs processed two at a time),
+    // Operand loads are software-pipelined by hand: the B pairs of k-pair
+    // kp+1 load while kp computes (two named buffers, k-pairs two at a time),
     // and each A row-pair loads one row-pair ahead of its use.
     const unsigned long long *Asl = &sm.As[st][0][0];
     const unsigned long long *Bsl = &sm.Bs[st][0][0];
-    auto load_b = [&](int kp, unsigned long long (&b)[8]) {
+    auto load_b = [&](int kp, unsigned long long (&b)[4]) {
 #pragma unroll
-      for (int cc = 0; cc < 8; cc += 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bsl[kp * T + col_at(cc, tx)]);
+      for (int cc = 0; cc < 4; cc += 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&Bsl[kp * H + col_at(cc, tx)]);
         b[cc] = t.x;
         b[cc + 1] = t.y;
       }
     };
-    auto compute = [&](int kp, const unsigned long long (&b)[8]) {
+    auto compute = [&](int kp, const unsigned long long (&b)[4]) {
       ulonglong2 an = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(0, ty)]);
 #pragma unroll
       for (int rp = 0; rp < 4; ++rp) {
         const ulonglong2 ac = an;
         if (rp < 3) an = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(2 * rp + 2, ty)]);
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
+        for (int cc = 0; cc < 4; ++cc) {
           mp32::relax2(acc[2 * rp][cc], ac.x, b[cc]);
           mp32::relax2(acc[2 * rp + 1][cc], ac.y, b[cc]);
         }
       }
     };
-    unsigned long long b0[8], b1[8];
+    unsigned long long b0[4], b1[4];
     load_b(0, b0);
 #pragma unroll 1
     for (int kp = 0; kp < KP; kp += 2) {
@@ -272,110 +275,102 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
     if (tid == 0 && s + STAGES < nslab) {
       fence_proxy_async_smem();
       const int s2 = s + STAGES;
-      mbar_expect_tx(&sm.bar[st], 2 * SLAB_BYTES);
-      bulk_g2s(&sm.As[st][0][0], srcA + (int64_t)s2 * KP * T, SLAB_BYTES, &sm.bar[st]);
-      bulk_g2s(&sm.Bs[st][0][0], srcB + (int64_t)s2 * KP * T, SLAB_BYTES, &sm.bar[st]);
+      mbar_expect_tx(&sm.bar[st], A_SLAB + B_SLAB);
+      bulk_g2s(&sm.As[st][0][0], srcA + (int64_t)s2 * KP * T, A_SLAB, &sm.bar[st]);
+      bulk_g2s(&sm.Bs[st][0][0], srcB + (int64_t)s2 * KP * H, B_SLAB, &sm.bar[st]);
     }
   }
 
-  // Epilogue.  The ring is free now: the block of new candidates goes to
-  // shared memory so that the rest runs as compact rolled loops with each
-  // warp owning 16 whole rows (lane l: columns 4l..4l+3), which keeps the
-  // code small (instruction-cache friendly) and every global access coalesced.
-  float *Cs = reinterpret_cast<float *>(smem_raw);  // [T][T]
+  // Epilogue.  The ring is free now: the half block of new candidates goes to
+  // shared memory so that the rest runs as compact loops with each warp
+  // owning 16 whole rows (lane l: columns 2l, 2l+1), which keeps the code small
+  // (instruction-cache friendly) and every global access coalesced.
+  float *Cs = reinterpret_cast<float *>(smem_raw);  // [T][H]
   __syncthreads();
 #pragma unroll
   for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
-    for (int cc = 0; cc < 8; cc += 2)
-      *reinterpret_cast<float2 *>(&Cs[row_at(rr, ty) * T + col_at(cc, tx)]) =
+    for (int cc = 0; cc < 4; cc += 2)
+      *reinterpret_cast<float2 *>(&Cs[row_at(rr, ty) * H + col_at(cc, tx)]) =
           make_float2(acc[rr][cc], acc[rr][cc + 1]);
   __syncthreads();
   const float *acp = pan.Acp + (int64_t)I * T * T;
-  const float *bt = pan.Bt + (int64_t)J * T * T;
-  const int w = tid >> 5, j0 = 4 * lane, i0 = w * 16;
-  const bool vec = vec_ok && j0 + 3 < mJ;
+  const float *bt = pan.Bt + ((int64_t)J * T + hJ * H) * T;
+  const int w = tid >> 5, j0 = 2 * lane, i0 = w * 16;
+  const bool vec = vec_ok && j0 + 1 < mJ;
   // Pass 1 (unrolled): all 16 old rows of the warp are loaded before any is
   // used (one memory round trip), improvements are flagged and written.
-  float4 o[16];
+  float2 o[16];
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
     const float *row = D + (int64_t)(baseI + i0 + t) * ld + baseJ;
-    o[t] = make_float4(INF, INF, INF, INF);
+    o[t] = make_float2(INF, INF);
     if (i0 + t < mI) {
       if (vec) {
-        o[t] = *reinterpret_cast<const float4 *>(row + j0);
+        o[t] = *reinterpret_cast<const float2 *>(row + j0);
       } else {
         if (j0 < mJ) o[t].x = row[j0];
         if (j0 + 1 < mJ) o[t].y = row[j0 + 1];
-        if (j0 + 2 < mJ) o[t].z = row[j0 + 2];
-        if (j0 + 3 < mJ) o[t].w = row[j0 + 3];
       }
     }
   }
-  unsigned long long flags = 0ull;  // bit 4t + q: row i0 + t, column j0 + q improved
+  unsigned flags = 0u;  // bit 2t + q: row i0 + t, column j0 + q improved
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
     if (i0 + t >= mI) continue;
-    const float4 c = *reinterpret_cast<const float4 *>(&Cs[(i0 + t) * T + j0]);
+    const float2 c = *reinterpret_cast<const float2 *>(&Cs[(i0 + t) * H + j0]);
     unsigned imp = 0u;
     if (j0 < mJ && c.x < o[t].x) imp |= 1u;
     if (j0 + 1 < mJ && c.y < o[t].y) imp |= 2u;
-    if (j0 + 2 < mJ && c.z < o[t].z) imp |= 4u;
-    if (j0 + 3 < mJ && c.w < o[t].w) imp |= 8u;
     if (!imp) continue;
-    flags |= (unsigned long long)imp << (4 * t);
+    flags |= imp << (2 * t);
     float *row = D + (int64_t)(baseI + i0 + t) * ld + baseJ;
     if (vec) {
-      *reinterpret_cast<float4 *>(row + j0) = make_float4(imp & 1 ? c.x : o[t].x, imp & 2 ? c.y : o[t].y,
-                                                          imp & 4 ? c.z : o[t].z, imp & 8 ? c.w : o[t].w);
+      *reinterpret_cast<float2 *>(row + j0) = make_float2(imp & 1 ? c.x : o[t].x, imp & 2 ? c.y : o[t].y);
     } else {
       if (imp & 1) row[j0] = c.x;
       if (imp & 2) row[j0 + 1] = c.y;
-      if (imp & 4) row[j0 + 2] = c.z;
-      if (imp & 8) row[j0 + 3] = c.w;
     }
   }
   if (!P) return;
   // Pass 2: P for every improved output.  The warp walks its improved outputs
-  // (all rows, all lanes) as one stream, eight at a time: the A-row and B-row
-  // loads of the eight are issued together (one memory round trip per group),
+  // (all rows, all lanes) as one stream, four at a time: the A-row and B-row
+  // loads of the four are issued together (one memory round trip per group),
   // then for each output lane l tests k = 4l..4l+3 and the lowest hit wins.
-  unsigned long long wf = __reduce_or_sync(kFullMask, (unsigned)(flags >> 32));
-  wf = (wf << 32) | __reduce_or_sync(kFullMask, (unsigned)flags);
+  unsigned wf = __reduce_or_sync(kFullMask, flags);
   unsigned bal = 0u;
   int pos = 0;
   auto next = [&](int &t, int &sj) -> bool {  // warp-uniform
     while (!bal) {
       if (!wf) return false;
-      pos = __ffsll((long long)wf) - 1;
+      pos = __ffs(wf) - 1;
       wf &= wf - 1;
-      bal = __ballot_sync(kFullMask, (flags >> pos) & 1ull);
+      bal = __ballot_sync(kFullMask, (flags >> pos) & 1u);
     }
     const int src = __ffs(bal) - 1;
     bal &= bal - 1;
-    t = pos >> 2;
-    sj = 4 * src + (pos & 3);
+    t = pos >> 1;
+    sj = 2 * src + (pos & 1);
     return true;
   };
 #pragma unroll 1
   for (;;) {
-    int t[8], sj[8];
-    bool v[8];
+    int t[4], sj[4];
+    bool v[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = next(t[u], sj[u]);
+    for (int u = 0; u < 4; ++u) v[u] = next(t[u], sj[u]);
     if (!v[0]) break;
-    float4 av[8], bv[8];
-    float tg[8];
+    float4 av[4], bv[4];
+    float tg[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 4; ++u) {
       if (!v[u]) continue;
       av[u] = reinterpret_cast<const float4 *>(acp + (i0 + t[u]) * T)[lane];
       bv[u] = reinterpret_cast<const float4 *>(bt + sj[u] * T)[lane];
-      tg[u] = Cs[(i0 + t[u]) * T + sj[u]];
+      tg[u] = Cs[(i0 + t[u]) * H + sj[u]];
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 4; ++u) {
       if (!v[u]) continue;
       const float g = tg[u];
       const unsigned h = (__fadd_rn(av[u].x, bv[u].x) == g ? 1u : 0u) |
@@ -462,8 +457,8 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
         k2<<<2 * (R - 1), kK2Threads, smem2, s>>>(D, ld, P, n, r, R, pan);
       }
       PhaseScope ps(3, s);
-      fw_phase3_minplus_f32<<<(R - 1) * (R - 1), mp32::THREADS, sizeof(k3::Smem), s>>>(D, ld, P, n, r,
-                                                                                      R, vec_ok, pan);
+      fw_phase3_minplus_f32<<<2 * (R - 1) * (R - 1), mp32::THREADS, sizeof(k3::Smem), s>>>(
+          D, ld, P, n, r, R, vec_ok, pan);
     }
   }
   cudaError_t e = cudaGetLastError();
