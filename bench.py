@@ -163,9 +163,11 @@ def measured_peaks():
 
 
 def alu_peak_relax_per_s(sms: int, mhz: float) -> float:
-    """add+min peak: 128 relaxations / clock / SM (one packed FP32x2 add on the FMA
-    pipe plus one three-input min on the ALU pipe per two relaxations, one issue
-    slot per relaxation per lane) x SMs x clock."""
+    """add+min peak from unit counts: 128 relaxations / clock / SM (the FMA pipe
+    adds 128 lanes per clock, as one packed FP32x2 add per two relaxations, and
+    the ALU pipe compares 128 lanes per clock, as one three-input min per two
+    relaxations) x SMs x clock.  The measured rate of the instruction pair is
+    reported beside it (apsp_measure_peak); it is lower (~98 on GB300)."""
     return 128.0 * sms * mhz * 1e6
 
 

@@ -3,10 +3,12 @@
 //
 // The kernel runs the exact instruction pair of the FP32 inner loops - one
 // packed add.rn.f32x2 forming two candidates and one three-input min.f32
-// folding them into an accumulator - on 16 independent accumulators per
-// thread, with no memory traffic, and times itself with the SM clock.  The
-// FP64 variant runs the interval pair (add.rm + add.rp, two mins) that the
-// FP64 path uses per pair of relaxations.
+// folding them into an accumulator - on 16 independent chains per thread,
+// with no memory traffic, and times itself with the SM clock.  Every packed
+// add takes its previous result as an operand, so the compiler can neither
+// hoist nor merge adds (loop-invariant operands would let it, and the rate
+// would come out too high).  The FP64 variant runs the interval pair
+// (add.rm + add.rp, two mins) that the FP64 path uses per pair of relaxations.
 #include <stdint.h>
 
 #include "common.cuh"
@@ -17,14 +19,15 @@ template <int MODE>
 __global__ void __launch_bounds__(256) peak_kernel(float *out, unsigned long long *cycles, int iters) {
   constexpr int CH = 16;
   float acc[CH], acc2[CH];
-  unsigned long long a[CH];
-  const unsigned long long b = 0x3f8000003f800000ull;  // (1.0f, 1.0f)
+  unsigned long long t[CH], u[CH];
+  const unsigned long long c = 0x3380000033800000ull;  // (2^-24, 2^-24): the sums keep changing
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
     acc[j] = 1e30f;
     acc2[j] = 1e30f;
-    a[j] = ((unsigned long long)__float_as_uint((float)(threadIdx.x + 2 * j + 1)) << 32) |
+    t[j] = ((unsigned long long)__float_as_uint((float)(threadIdx.x + 2 * j + 1)) << 32) |
            __float_as_uint((float)(threadIdx.x + 2 * j));
+    u[j] = t[j];
   }
   __syncthreads();
   const unsigned long long t0 = clock64();
@@ -32,29 +35,26 @@ __global__ void __launch_bounds__(256) peak_kernel(float *out, unsigned long lon
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
       if (MODE == 0) {
-        asm volatile(
-            "{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
-            "add.rn.f32x2 t, %1, %2;\n\tmov.b64 {lo, hi}, t;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
-            : "+f"(acc[j])
-            : "l"(a[j]), "l"(b));
+        asm volatile("add.rn.f32x2 %0, %0, %1;" : "+l"(t[j]) : "l"(c));
+        asm volatile("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
+                     : "+f"(acc[j])
+                     : "l"(t[j]));
       } else {  // lower and upper bound of the same two candidates
-        asm volatile(
-            "{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
-            "add.rm.f32x2 t, %1, %2;\n\tmov.b64 {lo, hi}, t;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
-            : "+f"(acc[j])
-            : "l"(a[j]), "l"(b));
-        asm volatile(
-            "{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
-            "add.rp.f32x2 t, %1, %2;\n\tmov.b64 {lo, hi}, t;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
-            : "+f"(acc2[j])
-            : "l"(a[j]), "l"(b));
+        asm volatile("add.rm.f32x2 %0, %0, %1;" : "+l"(t[j]) : "l"(c));
+        asm volatile("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
+                     : "+f"(acc[j])
+                     : "l"(t[j]));
+        asm volatile("add.rp.f32x2 %0, %0, %1;" : "+l"(u[j]) : "l"(c));
+        asm volatile("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
+                     : "+f"(acc2[j])
+                     : "l"(u[j]));
       }
     }
   }
   const unsigned long long t1 = clock64();
   float s = 0.f;
 #pragma unroll
-  for (int j = 0; j < CH; ++j) s += acc[j] + acc2[j];
+  for (int j = 0; j < CH; ++j) s += acc[j] + acc2[j] + __uint_as_float((unsigned)t[j]) + __uint_as_float((unsigned)u[j]);
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }

@@ -233,3 +233,15 @@ def test_phase_timing_hook_and_device_status():
     assert prof["phase1_diag"][1] == R and prof["phase2_panels"][1] == R and prof["phase3_minplus"][1] == R
     assert all(ms >= 0 for ms, _ in prof.values())
     assert apsp.device_status() == apsp.APSP_OK
+
+
+def test_measured_pair_rate_is_plausible():
+    """The inner-loop instruction pair sustains close to the 128 relaxations per
+    clock per SM of the issue model (FP32), and about half of that for the FP64
+    interval pair; bad arguments are rejected."""
+    r32 = apsp.measure_peak(4)
+    r64 = apsp.measure_peak(8)
+    assert 64.0 < r32 <= 132.0, r32
+    assert 0.35 * r32 < r64 < 0.75 * r32, (r32, r64)
+    with pytest.raises(apsp.ApspError):
+        apsp.measure_peak(2)
