@@ -71,7 +71,16 @@ APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm,
   if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int blocks = sms * 4, threads = 256, iters = 4096;
+  // One wave of blocks, all resident together, so that the slowest block's
+  // clock count covers every block's work (the FP64 variant holds more
+  // registers and fits fewer blocks per SM than the FP32 one).
+  const int threads = 256, iters = 4096;
+  int per_sm = 0;
+  const cudaError_t oe =
+      dtype_bytes == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel<0>, threads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel<1>, threads, 0);
+  if (oe != cudaSuccess || per_sm < 1) return APSP_ECUDA;
+  const int blocks = sms * (per_sm < 4 ? per_sm : 4);
   float *out = nullptr;
   unsigned long long *cyc = nullptr;
   cudaGetLastError();
@@ -96,8 +105,8 @@ APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm,
   unsigned long long mx = 1;
   for (int i = 0; i < blocks; ++i) mx = h[i] > mx ? h[i] : mx;
   delete[] h;
-  // all blocks are resident at once (4 x 256 threads per SM); relaxations per
-  // pair-instruction: 2 (FP32) or 2 FP64 relaxations per interval pair.
+  // all blocks are resident at once; relaxations per pair-instruction: 2
+  // (FP32) or 2 FP64 relaxations per interval pair.
   const double relax = 2.0 * 16.0 * iters * (double)threads * blocks;
   *relax_per_clk_per_sm = relax / sms / (double)mx;
   return APSP_OK;
