@@ -203,6 +203,15 @@ int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm, void *strea
 int apsp_device_status(void *stream);
 int apsp_profile_collect(double *ms, int64_t *launches);
 
+/* The same records one by one, in launch order (per-round timing: the r-th
+ * phase-4 record is round r of the last solve when one solve was recorded).
+ * Waits for the recorded events; writes min(cap, records) entries to
+ * phase[] (index as above) and ms[] (device time of that launch), and the
+ * number of records to *count.  phase and ms may be NULL when cap is 0.
+ * Returns APSP_EINVAL for a NULL count, a negative cap, or NULL arrays with
+ * cap > 0. */
+int apsp_profile_records(int32_t *phase, float *ms, int64_t cap, int64_t *count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -44,6 +44,8 @@ SIGNATURES = {
     "apsp_device_status": (ctypes.c_int, [_p]),
     "apsp_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _p]),
     "apsp_profile_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
+    "apsp_profile_records": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                            _i64, ctypes.POINTER(_i64)]),
 }
 
 _lock = threading.Lock()
@@ -169,6 +171,18 @@ def profile_collect() -> dict:
     cnt = (ctypes.c_int64 * 4)()
     _check(load().apsp_profile_collect(ms, cnt), "apsp_profile_collect")
     return {PHASES[p]: (float(ms[p]), int(cnt[p])) for p in range(4)}
+
+
+def profile_records() -> list:
+    """[(phase, ms)] of every recorded launch, in launch order."""
+    lib = load()
+    count = _i64(0)
+    _check(lib.apsp_profile_records(None, None, 0, ctypes.byref(count)), "apsp_profile_records")
+    cap = int(count.value)
+    ph = (ctypes.c_int32 * max(cap, 1))()
+    ms = (ctypes.c_float * max(cap, 1))()
+    _check(lib.apsp_profile_records(ph, ms, cap, ctypes.byref(count)), "apsp_profile_records")
+    return [(PHASES[ph[i]], float(ms[i])) for i in range(min(cap, int(count.value)))]
 
 
 from .batched import BatchedPlan, apsp_fw_batched_f32, apsp_fw_batched  # noqa: E402

@@ -177,6 +177,11 @@ __global__ void __launch_bounds__(mp32::THREADS)
 namespace k3 {
 constexpr int T = mp32::T, KS = mp32::KS, KP = mp32::KP, STAGES = 2, H = T / 2;
 constexpr uint32_t A_SLAB = KP * T * 8, B_SLAB = KP * H * 8;
+#ifndef APSP_K3_DENSE_MIN
+#define APSP_K3_DENSE_MIN 96
+#endif
+// Improved outputs (of 512) above which an 8-row group takes recovery pass 2a.
+constexpr int kDenseMin = APSP_K3_DENSE_MIN;
 struct Smem {
   unsigned long long As[STAGES][KP][T];  // As[kp][i] = (A[i][2kp], A[i][2kp+1])
   unsigned long long Bs[STAGES][KP][H];  // Bs[kp][j] = (B[2kp][j], B[2kp+1][j]), this half
@@ -333,7 +338,89 @@ __global__ void __launch_bounds__(mp32::THREADS, 3)
     }
   }
   if (!P) return;
-  // Pass 2: P for every improved output.  The warp walks its improved outputs
+  // Pass 2a: each 8-row group of the warp with many improved outputs (the
+  // early rounds, where most outputs improve) is resolved lane-parallel: lane
+  // l scans the 128 candidates of its own two columns in the paired panel
+  // layout the main loop read (B pairs coalesced, A pairs broadcast), folds
+  // every 8 k into one minimum with three-input mins, keeps the lowest 8-k
+  // chunk whose minimum equals the output's new value, and finds the first
+  // such k inside that chunk.  The operands stream from L2 once per group
+  // instead of once per improved output.
+  {
+    const unsigned long long *pa = srcA + i0, *pb = srcB + j0;
+#pragma unroll 1
+    for (int G = 0; G < 2; ++G) {
+      const unsigned gm = 0xFFFFu << (16 * G);
+      if ((int)__reduce_add_sync(kFullMask, (unsigned)__popc(flags & gm)) < kDenseMin) continue;
+      const int tg0 = 8 * G;
+      float g[8][2];
+      unsigned hit[8];  // bit c (+16 for column j0 + 1): chunk c's minimum equals g
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float2 c = *reinterpret_cast<const float2 *>(&Cs[(i0 + tg0 + t) * H + j0]);
+        g[t][0] = c.x;
+        g[t][1] = c.y;
+        hit[t] = 0u;
+      }
+#pragma unroll 1
+      for (int c = T / 8 - 1; c >= 0; --c) {
+        ulonglong2 b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = __ldg(reinterpret_cast<const ulonglong2 *>(pb + (4 * c + q) * H));
+        const unsigned bit = 1u << c;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          unsigned long long a[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a[q] = __ldg(pa + (4 * c + q) * T + tg0 + t);
+#pragma unroll
+          for (int q2 = 0; q2 < 2; ++q2) {
+            float2 s0 = mp32::sum2(a[0], q2 ? b[0].y : b[0].x), s1 = mp32::sum2(a[1], q2 ? b[1].y : b[1].x);
+            float2 s2 = mp32::sum2(a[2], q2 ? b[2].y : b[2].x), s3 = mp32::sum2(a[3], q2 ? b[3].y : b[3].x);
+            float m = mp32::min3f(s0.x, s0.y, s1.x);
+            m = mp32::min3f(m, s1.y, s2.x);
+            m = mp32::min3f(m, s2.y, s3.x);
+            m = fminf(m, s3.y);
+            if (m == g[t][q2]) hit[t] |= bit << (16 * q2);
+          }
+        }
+      }
+      // Resolution: both outputs of a row load their chunk's eight operand
+      // pairs at once (one memory round trip per row); a descending select
+      // chain keeps the first k whose sum equals g.
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const unsigned fl = (flags >> (2 * (tg0 + t))) & 3u;
+        if (!fl) continue;
+        int c[2];
+        unsigned long long av[2][4], bv[2][4];
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+          // an improved output's chunk mask is not empty: g is one of the sums
+          c[q2] = ((fl >> q2) & 1u) ? __ffs((hit[t] >> (16 * q2)) & 0xFFFFu) - 1 : 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            av[q2][q] = __ldg(pa + (4 * c[q2] + q) * T + tg0 + t);
+            bv[q2][q] = __ldg(pb + (4 * c[q2] + q) * H + q2);
+          }
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+          if (!((fl >> q2) & 1u)) continue;
+          int k = 8 * c[q2] + 7;
+#pragma unroll
+          for (int q = 3; q >= 0; --q) {
+            const float2 sv = mp32::sum2(av[q2][q], bv[q2][q]);
+            k = sv.y == g[t][q2] ? 8 * c[q2] + 2 * q + 1 : k;
+            k = sv.x == g[t][q2] ? 8 * c[q2] + 2 * q : k;
+          }
+          P[(int64_t)(baseI + i0 + tg0 + t) * ld + baseJ + j0 + q2] = baseK + k;
+        }
+      }
+      flags &= ~gm;
+    }
+  }
+  // Pass 2b: P for every remaining improved output.  The warp walks them
   // (all rows, all lanes) as one stream, four at a time: the A-row and B-row
   // loads of the four are issued together (one memory round trip per group),
   // then for each output lane l tests k = 4l..4l+3 and the lowest hit wins.
@@ -508,11 +595,13 @@ APSP_EXPORT int apsp_version(void) { return 100; }
 
 APSP_EXPORT int apsp_profile_enable(int on) {
   std::lock_guard<std::mutex> g(apsp::g_prof_mu);
-  for (auto &r : apsp::g_prof_recs) {
-    apsp::g_prof_pool.push_back(r.a);
-    apsp::g_prof_pool.push_back(r.b);
+  if (on) {  // a new recording starts: recycle the old records' events
+    for (auto &r : apsp::g_prof_recs) {
+      apsp::g_prof_pool.push_back(r.a);
+      apsp::g_prof_pool.push_back(r.b);
+    }
+    apsp::g_prof_recs.clear();
   }
-  apsp::g_prof_recs.clear();
   apsp::g_prof_on = on != 0;
   return APSP_OK;
 }
@@ -531,6 +620,24 @@ APSP_EXPORT int apsp_profile_collect(double *ms, int64_t *launches) {
     ms[r.phase] += t;
     launches[r.phase] += 1;
   }
+  return APSP_OK;
+}
+
+APSP_EXPORT int apsp_profile_records(int32_t *phase, float *ms, int64_t cap, int64_t *count) {
+  if (!count || cap < 0 || (cap > 0 && (!phase || !ms))) return APSP_EINVAL;
+  std::lock_guard<std::mutex> g(apsp::g_prof_mu);
+  int64_t i = 0;
+  for (auto &r : apsp::g_prof_recs) {
+    if (i < cap) {
+      if (cudaEventSynchronize(r.b) != cudaSuccess) return APSP_ECUDA;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return APSP_ECUDA;
+      phase[i] = r.phase;
+      ms[i] = t;
+    }
+    ++i;
+  }
+  *count = i;
   return APSP_OK;
 }
 

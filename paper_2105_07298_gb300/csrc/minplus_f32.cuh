@@ -48,6 +48,19 @@ __device__ __forceinline__ void relax2(float &acc, unsigned long long a, unsigne
       : "l"(a), "l"(b));
 }
 
+// The two candidate sums of relax2, unfolded (same rounding).
+__device__ __forceinline__ float2 sum2(unsigned long long a, unsigned long long b) {
+  unsigned long long t;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(b));
+  return make_float2(__uint_as_float((unsigned)t), __uint_as_float((unsigned)(t >> 32)));
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
   return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
 }

@@ -232,6 +232,10 @@ def test_phase_timing_hook_and_device_status():
     assert prof["path_init"][1] == 1
     assert prof["phase1_diag"][1] == R and prof["phase2_panels"][1] == R and prof["phase3_minplus"][1] == R
     assert all(ms >= 0 for ms, _ in prof.values())
+    recs = apsp.profile_records()
+    assert [p for p, _ in recs].count("phase3_minplus") == R and recs[0][0] == "path_init"
+    for ph, (ms, cnt) in prof.items():
+        assert sum(t for p, t in recs if p == ph) == pytest.approx(ms, rel=1e-4, abs=1e-4)
     assert apsp.device_status() == apsp.APSP_OK
 
 
