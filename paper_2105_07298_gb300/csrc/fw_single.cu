@@ -3,7 +3,7 @@
 // Schedule (§2.2 "Blocked FW Algorithm", kernels as in §3.2): the n x n
 // matrix is cut into TB x TB blocks; each of the R = ceil(n / TB) rounds runs
 //   K1  fw_phase1_diag      phase 1: the diagonal block (r,r), k sequential;
-//   K2  fw_phase2_panels    phases 2+3: the row blocks (r,J) and the column
+//   K2  fw_phase2_lines     phases 2+3: the row blocks (r,J) and the column
 //                           blocks (I,r), k sequential inside each block;
 //   K3  fw_phase3_minplus   phase 4: every other block (I,J) gets
 //                           C = min(C, A (x) B) with A = block (I,r) and
@@ -45,14 +45,20 @@ __global__ void fw_path_init(int32_t *__restrict__ P, int64_t n, int64_t ld) {
 }
 
 // --------------------------------------------------------------------------
-// K2: phases 2 and 3.  CTA b < R-1 owns row block (r, J), the others column
-// block (I, r).  The diagonal block (final after K1) and the own block sit in
-// shared memory (row stride T+1: row and column walks are both free of bank
-// conflicts); k runs sequentially over the round's vertices.
-//   row block:    own[i][j] = min(own[i][j], diag[i][k] + own[k][j])
-//   column block: own[i][j] = min(own[i][j], own[i][k] + diag[k][j])
-// When `pan` is given (FP32), the finished blocks are also written, padded
-// with +inf to full T x T, in the layouts phase 4 reads this round:
+// K2: phases 2 and 3.  Blocks b < R-1 of the grid cover row block (r, J),
+// the others column block (I, r); four CTAs share a block, 32 lines each.
+// Within a row block every column evolves on its own, within a column block
+// every row does:
+//   row block, column j:  own[i][j] = min(own[i][j], diag[i][k] + own[k][j])
+//   column block, row i:  own[i][j] = min(own[i][j], own[i][k] + diag[k][j])
+// for k ascending over the round's vertices (the diagonal block is final
+// after K1).  A warp keeps four such lines in registers, lane l holding
+// positions 2l, 2l+1, 2l+64, 2l+65 of each; at step k the owner of position k
+// broadcasts the line's current value with a shuffle, and the diagonal
+// entries come from shared memory (M[k][pos], transposed for row blocks) as
+// pairs, so one add.rn.f32x2 forms two candidates.  No barrier per step.
+// The finished blocks are also written, padded with +inf to T x T, in the
+// layouts phase 4 reads this round:
 //   row block (r,J):    Bpan[J][j/64][kp][j%64] = (own[2kp][j], own[2kp+1][j]),
 //                       Bt[J][j][k] = own[k][j]
 //   column block (I,r): Apan[I][kp][i] = (own[i][2kp], own[i][2kp+1]),
@@ -63,91 +69,97 @@ struct Panels {
   float *Acp, *Bt;
 };
 
-template <typename Real, int T, int THREADS>
-__global__ void __launch_bounds__(THREADS) fw_phase2_panels(Real *__restrict__ D, int64_t ld,
-                                                            int32_t *__restrict__ P, int n, int r,
-                                                            int R, Panels pan) {
-  constexpr int S = T + 1;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  Real *diag = reinterpret_cast<Real *>(smem_raw);
-  Real *own = diag + T * S;
-  constexpr int EPT = T * T / THREADS;
-  const int b = blockIdx.x;
+namespace k2 {
+constexpr int T = mp32::T, THREADS = 256, LINES = 4, PARTS = T / (THREADS / 32 * LINES), MS = T + 2;
+constexpr int SMEM = T * MS * 4;
+}  // namespace k2
+
+__global__ void __launch_bounds__(k2::THREADS, 2) fw_phase2_lines_f32(float *__restrict__ D, int64_t ld,
+                                                                  int32_t *__restrict__ P, int n, int r,
+                                                                  int R, Panels pan) {
+  using namespace k2;
+  extern __shared__ __align__(16) float M[];  // [T][MS]
+  const int b = blockIdx.x / PARTS, part = blockIdx.x % PARTS;
   const bool is_row = b < R - 1;
   int other = is_row ? b : b - (R - 1);
   other += (other >= r);
   const int base_r = r * T, m_r = min(T, n - base_r);
   const int base_o = other * T, m_o = min(T, n - base_o);
-  // own block: rows x cols = (m_r x m_o) for a row block, (m_o x m_r) for a column block
-  const int rows = is_row ? m_r : m_o, cols = is_row ? m_o : m_r;
-  const int64_t row0 = is_row ? base_r : base_o, col0 = is_row ? base_o : base_r;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const float INF = inf<float>();
   for (int e = tid; e < T * T; e += THREADS) {
-    const int i = e / T, j = e % T;
-    diag[i * S + j] = (i < m_r && j < m_r) ? D[(int64_t)(base_r + i) * ld + base_r + j] : inf<Real>();
-    own[i * S + j] = (i < rows && j < cols) ? D[(row0 + i) * ld + col0 + j] : inf<Real>();
+    const int i = e / T, k = e % T;
+    const float x = (i < m_r && k < m_r) ? D[(int64_t)(base_r + i) * ld + base_r + k] : INF;
+    M[is_row ? k * MS + i : i * MS + k] = x;  // M[k][pos]
   }
-  int pk[EPT];
+  const int line0 = part * (T / PARTS) + w * LINES;
+  // Element (line, pos) of the own block sits at D[g0 + line * sl + pos * sp].
+  const int64_t g0 = is_row ? (int64_t)base_r * ld + base_o : (int64_t)base_o * ld + base_r;
+  const int64_t sl = is_row ? 1 : ld, sp = is_row ? ld : 1;
+  // lane's positions along a line: pos(s) = 2 lane + (s & 1) + 64 (s >> 1)
+  float v[LINES][4];
+  unsigned pk[LINES];  // byte q: round-local k of the last improvement of slot q, 0xFF: none
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) pk[q] = -1;
+  for (int c = 0; c < LINES; ++c) {
+    pk[c] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int line = line0 + c, pos = 2 * lane + (q & 1) + 64 * (q >> 1);
+      v[c][q] = (line < m_o && pos < m_r) ? D[g0 + line * sl + pos * sp] : INF;
+    }
+  }
   __syncthreads();
-  if (is_row) {
-    for (int k = 0; k < m_r; ++k) {
+  // Step k: owner lane (k mod 64) / 2, slot 2 (k / 64) + (k mod 2).
 #pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * THREADS;
-        const int i = e / T, j = e % T;
-        const Real cand = add_rn(diag[i * S + k], own[k * S + j]);
-        if (cand < own[i * S + j]) {
-          own[i * S + j] = cand;
-          pk[q] = base_r + k;
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+    for (int kk = 0; kk < 32; ++kk) {
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        const int k = 64 * h + 2 * kk + par;
+        const unsigned long long m01 = *reinterpret_cast<const unsigned long long *>(&M[k * MS + 2 * lane]);
+        const unsigned long long m23 = *reinterpret_cast<const unsigned long long *>(&M[k * MS + 64 + 2 * lane]);
+#pragma unroll
+        for (int c = 0; c < LINES; ++c) {
+          const float vk = __shfl_sync(kFullMask, v[c][2 * h + par], kk);
+          const unsigned long long vv = mp32::pack2(vk, vk);
+          const float2 c01 = mp32::sum2(m01, vv), c23 = mp32::sum2(m23, vv);
+          const float cand[4] = {c01.x, c01.y, c23.x, c23.y};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (cand[q] < v[c][q]) {
+              v[c][q] = cand[q];
+              pk[c] = __byte_perm(pk[c], (unsigned)k, 0x3210 ^ ((0x3210 & (0xF << (4 * q))) ^ (4 << (4 * q))));
+            }
         }
       }
-      __syncthreads();
-    }
-  } else {
-    for (int k = 0; k < m_r; ++k) {
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = tid + q * THREADS;
-        const int i = e / T, j = e % T;
-        const Real cand = add_rn(own[i * S + k], diag[k * S + j]);
-        if (cand < own[i * S + j]) {
-          own[i * S + j] = cand;
-          pk[q] = base_r + k;
-        }
-      }
-      __syncthreads();
     }
   }
+  // D and P where the line improved; the phase-4 panels everywhere (padded).
+  const int64_t blk = other;
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * THREADS;
-    const int i = e / T, j = e % T;
-    if (i < rows && j < cols && pk[q] >= 0) {
-      const int64_t g = (row0 + i) * ld + col0 + j;
-      D[g] = own[i * S + j];
-      if (P) P[g] = pk[q];
-    }
-  }
-  if constexpr (sizeof(Real) == 4) {
-    if (pan.Apan) {
-      const float *o = reinterpret_cast<const float *>(own);
-      const int64_t blk = other;
-      for (int e = tid; e < T * T / 2; e += THREADS) {
-        const int kp = e / T, x = e % T;  // x = j (row block) or i (column block)
-        const float lo = is_row ? o[(2 * kp) * S + x] : o[x * S + 2 * kp];
-        const float hi = is_row ? o[(2 * kp + 1) * S + x] : o[x * S + 2 * kp + 1];
-        const unsigned long long v =
-            ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
-        if (is_row)  // two 64-wide halves, so a phase-4 CTA's B slab is contiguous
-          pan.Bpan[((blk * 2 + (x >> 6)) * (T / 2) + kp) * (T / 2) + (x & 63)] = v;
-        else
-          pan.Apan[(blk * (T / 2) + kp) * T + x] = v;
+  for (int c = 0; c < LINES; ++c) {
+    const int line = line0 + c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int pos = 2 * lane + (q & 1) + 64 * (q >> 1);
+      const unsigned kq = (pk[c] >> (8 * q)) & 0xFFu;
+      if (kq != 0xFFu) {  // improved: inside the matrix
+        const int64_t g = g0 + line * sl + pos * sp;
+        D[g] = v[c][q];
+        if (P) P[g] = base_r + (int)kq;
       }
-      for (int e = tid; e < T * T; e += THREADS) {
-        const int x = e / T, k = e % T;  // Bt[J][j][k] = own[k][j]; Acp[I][i][k] = own[i][k]
-        (is_row ? pan.Bt : pan.Acp)[(blk * T + x) * T + k] = is_row ? o[k * S + x] : o[x * S + k];
+    }
+#pragma unroll
+    for (int hq = 0; hq < 2; ++hq) {  // positions 2 lane + 64 hq + {0, 1}: k-pair kp = lane + 32 hq
+      const int kp = lane + 32 * hq;
+      const unsigned long long pr = mp32::pack2(v[c][2 * hq], v[c][2 * hq + 1]);
+      if (is_row) {
+        pan.Bpan[((blk * 2 + (line >> 6)) * (T / 2) + kp) * (T / 2) + (line & 63)] = pr;
+        *reinterpret_cast<float2 *>(&pan.Bt[(blk * T + line) * T + 2 * kp]) = make_float2(v[c][2 * hq], v[c][2 * hq + 1]);
+      } else {
+        pan.Apan[(blk * (T / 2) + kp) * T + line] = pr;
+        *reinterpret_cast<float2 *>(&pan.Acp[(blk * T + line) * T + 2 * kp]) = make_float2(v[c][2 * hq], v[c][2 * hq + 1]);
       }
     }
   }
@@ -484,7 +496,7 @@ std::vector<cudaEvent_t> g_prof_pool;
 // --------------------------------------------------------------------------
 constexpr int kMaxN = 65536;
 
-constexpr int kT32 = mp32::T, kT64 = 128, kK2Threads = 1024;
+constexpr int kT32 = mp32::T, kT64 = 128;
 static int g_smem_p2f[64], g_smem_k3[64];
 
 int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s);
@@ -510,9 +522,7 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
   const int n = (int)n64;
   constexpr int T = kT32;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int smem2 = 2 * T * (T + 1) * (int)sizeof(float);
-  auto k2 = fw_phase2_panels<float, T, kK2Threads>;
-  if ((st = ensure_smem(k2, smem2, g_smem_p2f))) return st;
+  if ((st = ensure_smem(fw_phase2_lines_f32, k2::SMEM, g_smem_p2f))) return st;
   if ((st = ensure_smem(fw_phase3_minplus_f32, (int)sizeof(k3::Smem), g_smem_k3))) return st;
   cudaGetLastError();  // clear any stale error so the checks below are ours
   const int R = (n + T - 1) / T;
@@ -541,7 +551,7 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
     if (R > 1) {
       {
         PhaseScope ps(2, s);
-        k2<<<2 * (R - 1), kK2Threads, smem2, s>>>(D, ld, P, n, r, R, pan);
+        fw_phase2_lines_f32<<<2 * (R - 1) * k2::PARTS, k2::THREADS, k2::SMEM, s>>>(D, ld, P, n, r, R, pan);
       }
       PhaseScope ps(3, s);
       fw_phase3_minplus_f32<<<2 * (R - 1) * (R - 1), mp32::THREADS, sizeof(k3::Smem), s>>>(
