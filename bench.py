@@ -167,7 +167,7 @@ def alu_peak_relax_per_s(sms: int, mhz: float) -> float:
     adds 128 lanes per clock, as one packed FP32x2 add per two relaxations, and
     the ALU pipe compares 128 lanes per clock, as one three-input min per two
     relaxations) x SMs x clock.  The measured rate of the instruction pair is
-    reported beside it (apsp_measure_peak); it is lower (~98 on GB300)."""
+    reported beside it (apsp_measure_peak); it is lower (~89 on GB300)."""
     return 128.0 * sms * mhz * 1e6
 
 
@@ -179,21 +179,21 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(n: int):
-    """dram bytes per phase-4 launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """dram bytes of phase 4 per round (its one or two launches) from the
+    committed ncu summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "phase3_minplus_f32_traffic.txt")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m_hash = re.search(r"kernel_source_hash:\s*(\w+)", txt)
-    m_bpl = re.search(r"dram_bytes_per_launch_n%d:\s*([0-9.eE+]+)" % n, txt)
+    m_bpl = re.search(r"dram_bytes_per_round_n%d:\s*([0-9.eE+]+)" % n, txt)
     if not m_hash or not m_bpl or m_hash.group(1) != kernel_source_hash():
         return None
     return float(m_bpl.group(1))
 
 
-def phase3_relax_per_launch(n: int, T: int) -> float:
-    """Algorithmic relaxations of one phase-4 launch, averaged over the rounds:
+def phase3_relax_per_round(n: int, T: int) -> float:
+    """Algorithmic phase-4 relaxations of one round, averaged over the rounds:
     round r updates every (i, j) outside block row/column r with every k of block r."""
     R = (n + T - 1) // T
     tot = 0
@@ -320,17 +320,29 @@ def bench_e2e(torch, apsp, graphgen, W_dev, args):
     D = torch.empty((n, n), dtype=torch.float32, device=W_dev.device)
     P = torch.empty((n, n), dtype=torch.int32, device=W_dev.device)
 
+    reps = max(1, min(args.steps, 2))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps + 1)]
+    it = iter(range(reps + 1))
+
     def step():
+        e = ev[next(it)]
         D.copy_(Wh, non_blocking=True)
+        e[0].record()
         apsp.apsp_fw_f32(D, P)
+        e[1].record()
         Dh.copy_(D, non_blocking=True)
         Ph.copy_(P, non_blocking=True)
+        e[2].record()
 
     step()
     torch.cuda.synchronize()
-    t = time_events(torch, step, max(1, min(args.steps, 2)))
-    reps = max(1, min(args.steps, 2))
-    return n ** 3 / (t / reps), n * n * 4, n * n * 8, Wh
+    t = time_events(torch, step, reps)
+    # parts of the timed steps: the solve, and the copies around it
+    solve = sum(e[0].elapsed_time(e[1]) for e in ev[1:]) / reps
+    d2h = sum(e[1].elapsed_time(e[2]) for e in ev[1:]) / reps
+    parts = {"step_ms": 1e3 * t / reps, "solve_ms": solve, "d2h_ms": d2h,
+             "h2d_ms": 1e3 * t / reps - solve - d2h}
+    return n ** 3 / (t / reps), n * n * 4, n * n * 8, Wh, parts
 
 
 def bench_fp64(torch, apsp, graphgen, args, dev):
@@ -496,10 +508,14 @@ def run_ours(args):
     value = total_relax / t_max
 
     T = apsp.block_size(torch.float64 if args.dtype == "f64" else torch.float32)
+    # Phase 4 of a round is one launch, or two (row/column r+1 first, then the
+    # rest) when the next round's phases 1-3 run beside it; its device time is
+    # summed per round.
     k3_ms, k3_launches = prof["phase3_minplus"]
-    per_launch_s = (k3_ms / 1e3) / max(k3_launches, 1)
-    relax_launch = phase3_relax_per_launch(n, T)
-    achieved = 2 * relax_launch / per_launch_s / 1e12  # Eq. 1 FLOP/s (add + compare)
+    rounds = ((n + T - 1) // T) * args.steps
+    per_round_s = (k3_ms / 1e3) / max(rounds, 1)
+    relax_round = phase3_relax_per_round(n, T)
+    achieved = 2 * relax_round / per_round_s / 1e12  # Eq. 1 FLOP/s (add + compare)
     # FP64 runs two FP32 interval relaxations (lower and upper bound) per FP64
     # relaxation on the same pipes: its bound is half the FP32 add+min peak.
     per_clk = 64.0 if args.dtype == "f64" else 128.0
@@ -523,11 +539,11 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic,
                      "flop_def": "Eq. 1: 2 FLOP (add + compare) per relaxation; "
-                                 f"{relax_launch:.4e} relaxations per launch (average over rounds)",
+                                 f"{relax_round:.4e} relaxations per round (average over rounds)",
                      "peak_basis": f"{facts['sms']} SMs x {per_clk:.0f} relax/clk/SM x {max_mhz:.0f} MHz (max SM clock)",
                      "frac_at_measured_clock": (achieved / (2 * alu_peak_relax_per_s(facts['sms'], mhz_meas)
                                                             * per_clk / 128.0 / 1e12) if mhz_meas else None),
-                     "avg_launch_ms": per_launch_s * 1e3, "launches": k3_launches,
+                     "avg_round_ms": per_round_s * 1e3, "launches": k3_launches,
                      "measured_pair_rate_relax_per_clk_sm": rate_meas,
                      "frac_of_measured_pair_rate": (achieved / (2 * rate_meas * facts["sms"] * max_mhz * 1e6 / 1e12)
                                                     if rate_meas else None)},
@@ -546,9 +562,9 @@ def run_ours(args):
     if rank == 0 and not args.no_extras and args.dtype == "f32":
         del D
         torch.cuda.empty_cache()
-        e2e_value, h2d, d2h, Wh = bench_e2e(torch, apsp, graphgen, W, args)
+        e2e_value, h2d, d2h, Wh, parts = bench_e2e(torch, apsp, graphgen, W, args)
         line["e2e"] = {"value": e2e_value * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h}
+                       "d2h_bytes_per_step": d2h, "parts_ms": parts}
         del W, P
         torch.cuda.empty_cache()
         if args.fp64_n > 0:
@@ -557,8 +573,9 @@ def run_ours(args):
             line["fp64"] = {"n": n64, "value": n64 ** 3 / t64, "unit": UNIT, "ms": 1e3 * t64,
                             "path_matrix": True, "steps": args.fp64_steps,
                             "phase_time_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof64.items()},
-                            "phase3_relax_per_s": phase3_relax_per_launch(n64, apsp.block_size(torch.float64))
-                            * k3[1] / args.fp64_steps / (k3[0] / 1e3 / args.fp64_steps)}
+                            "phase3_relax_per_s": phase3_relax_per_round(n64, apsp.block_size(torch.float64))
+                            * ((n64 + apsp.block_size(torch.float64) - 1) // apsp.block_size(torch.float64))
+                            / (k3[0] / 1e3 / args.fp64_steps)}
         torch.cuda.empty_cache()
         line["batched"] = bench_batched(torch, apsp, graphgen, args, dev)
         torch.cuda.empty_cache()

@@ -188,6 +188,10 @@ __global__ void __launch_bounds__(mp32::THREADS)
 // lane: the 128 candidate sums of an output in one memory round trip).
 namespace k3 {
 constexpr int T = mp32::T, KS = mp32::KS, KP = mp32::KP, STAGES = 2, H = T / 2;
+// Block sets of one phase-4 launch (grid: 2 CTAs per block).
+constexpr int kSetAll = 0;   // all (R-1)^2 blocks off row/column r
+constexpr int kSetNext = 1;  // the 2R-3 blocks in row r+1 or column r+1
+constexpr int kSetRest = 2;  // the (R-2)^2 blocks off rows/columns r and r+1
 constexpr uint32_t A_SLAB = KP * T * 8, B_SLAB = KP * H * 8;
 #ifndef APSP_K3_DENSE_MIN
 #define APSP_K3_DENSE_MIN 96
@@ -203,16 +207,37 @@ struct Smem {
 
 __global__ void __launch_bounds__(mp32::THREADS, 3)
     fw_phase3_minplus_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
-                          int R, int vec_ok, Panels pan) {
+                          int R, int vec_ok, Panels pan, int set) {
   using namespace k3;
   using mp32::col_at;
   using mp32::row_at;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   const int Rm = R - 1, tile = blockIdx.x >> 1, hJ = blockIdx.x & 1;
-  int I = tile / Rm, J = tile % Rm;
-  I += (I >= r);
-  J += (J >= r);
+  int I, J;
+  if (set == kSetAll) {  // every block off row and column r
+    I = tile / Rm;
+    J = tile % Rm;
+    I += (I >= r);
+    J += (J >= r);
+  } else if (set == kSetNext) {  // row r+1, then column r+1: the next round's K1/K2 input
+    if (tile < Rm) {
+      I = r + 1;
+      J = tile + (tile >= r);
+    } else {
+      I = tile - Rm;
+      I += (I >= r);
+      I += (I >= r + 1);
+      J = r + 1;
+    }
+  } else {  // the rest: rows and columns other than r and r+1
+    I = tile / (R - 2);
+    J = tile % (R - 2);
+    I += (I >= r);
+    I += (I >= r + 1);
+    J += (J >= r);
+    J += (J >= r + 1);
+  }
   const int baseI = I * T, baseJ = J * T + hJ * H, baseK = r * T;
   const int mI = min(T, n - baseI), mJ = min(H, n - baseJ), mK = min(T, n - baseK);
   if (mJ <= 0) return;  // empty half of the last (narrow) block; uniform exit
@@ -526,37 +551,83 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
   if ((st = ensure_smem(fw_phase3_minplus_f32, (int)sizeof(k3::Smem), g_smem_k3))) return st;
   cudaGetLastError();  // clear any stale error so the checks below are ours
   const int R = (n + T - 1) / T;
-  // Phase-4 operand panels, written by K2 each round (4 arrays of R*T*T
-  // 4-byte words); stream-ordered scratch, freed after the last round.
-  Panels pan{};
+  // Phase-4 operand panels, written by K2 each round: two sets (round parity)
+  // of 4 arrays of R*T*T 4-byte words, so that K2 of round r+1 can run while
+  // phase 4 of round r still reads round r's panels.  Stream-ordered scratch,
+  // freed after the last round.
+  Panels pan[2]{};
   char *scratch = nullptr;
   if (R > 1) {
     const size_t words = (size_t)R * T * T;
-    if (cudaMallocAsync((void **)&scratch, 4 * words * 4, s) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&scratch, 8 * words * 4, s) != cudaSuccess) {
       cudaGetLastError();
       return APSP_ENOMEM;
     }
-    pan.Apan = reinterpret_cast<unsigned long long *>(scratch);
-    pan.Bpan = reinterpret_cast<unsigned long long *>(scratch + words * 4);
-    pan.Acp = reinterpret_cast<float *>(scratch + 2 * words * 4);
-    pan.Bt = reinterpret_cast<float *>(scratch + 3 * words * 4);
+    for (int q = 0; q < 2; ++q) {
+      char *base = scratch + (size_t)q * 4 * words * 4;
+      pan[q].Apan = reinterpret_cast<unsigned long long *>(base);
+      pan[q].Bpan = reinterpret_cast<unsigned long long *>(base + words * 4);
+      pan[q].Acp = reinterpret_cast<float *>(base + 2 * words * 4);
+      pan[q].Bt = reinterpret_cast<float *>(base + 3 * words * 4);
+    }
   }
   if (P) path_init(P, n64, ld, s);
   const int vec_ok = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
-  for (int r = 0; r < R; ++r) {
+  auto diag_and_panels = [&](int r, cudaStream_t st) {
     {
-      PhaseScope ps(1, s);
-      fw_phase1_diag_f32<<<1, mp32::THREADS, 0, s>>>(D, ld, P, n, r);
+      PhaseScope ps(1, st);
+      fw_phase1_diag_f32<<<1, mp32::THREADS, 0, st>>>(D, ld, P, n, r);
     }
     if (R > 1) {
-      {
-        PhaseScope ps(2, s);
-        fw_phase2_lines_f32<<<2 * (R - 1) * k2::PARTS, k2::THREADS, k2::SMEM, s>>>(D, ld, P, n, r, R, pan);
-      }
-      PhaseScope ps(3, s);
-      fw_phase3_minplus_f32<<<2 * (R - 1) * (R - 1), mp32::THREADS, sizeof(k3::Smem), s>>>(
-          D, ld, P, n, r, R, vec_ok, pan);
+      PhaseScope ps(2, st);
+      fw_phase2_lines_f32<<<2 * (R - 1) * k2::PARTS, k2::THREADS, k2::SMEM, st>>>(D, ld, P, n, r, R, pan[r & 1]);
     }
+  };
+  auto phase4 = [&](int r, int set, int blocks) {
+    if (blocks <= 0) return;
+    PhaseScope ps(3, s);
+    fw_phase3_minplus_f32<<<2 * blocks, mp32::THREADS, sizeof(k3::Smem), s>>>(D, ld, P, n, r, R, vec_ok,
+                                                                             pan[r & 1], set);
+  };
+  // Look-ahead: phase 4 of round r first updates row and column r+1 (the
+  // blocks K1/K2 of round r+1 read), then the rest of the matrix while K1/K2
+  // of round r+1 run on a second, higher-priority stream; the two touch
+  // disjoint blocks and write/read different panel sets.
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_next = nullptr, ev_panels = nullptr;
+  if (R > 2) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_next, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_panels, cudaEventDisableTiming) != cudaSuccess) {
+      if (s2) cudaStreamDestroy(s2);
+      if (ev_next) cudaEventDestroy(ev_next);
+      if (scratch) cudaFreeAsync(scratch, s);
+      cudaGetLastError();
+      return APSP_ECUDA;
+    }
+  }
+  diag_and_panels(0, s);
+  for (int r = 0; r < R; ++r) {
+    if (R == 1) break;
+    if (r + 1 < R && s2) {
+      phase4(r, k3::kSetNext, 2 * R - 3);
+      cudaEventRecord(ev_next, s);
+      cudaStreamWaitEvent(s2, ev_next, 0);
+      diag_and_panels(r + 1, s2);
+      cudaEventRecord(ev_panels, s2);
+      phase4(r, k3::kSetRest, (R - 2) * (R - 2));
+      cudaStreamWaitEvent(s, ev_panels, 0);
+    } else {
+      phase4(r, k3::kSetAll, (R - 1) * (R - 1));
+      if (r + 1 < R) diag_and_panels(r + 1, s);
+    }
+  }
+  if (s2) {
+    cudaStreamDestroy(s2);
+    cudaEventDestroy(ev_next);
+    cudaEventDestroy(ev_panels);
   }
   cudaError_t e = cudaGetLastError();
   if (scratch) {

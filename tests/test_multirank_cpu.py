@@ -75,8 +75,8 @@ def test_phase3_relaxation_count_is_the_algorithmic_work():
     """Sum over the rounds of the phase-4 relaxations equals n^3 minus phases 1-3."""
     n, T = 1000, 128
     R = (n + T - 1) // T
-    per_launch = bench.phase3_relax_per_launch(n, T)
-    phase4 = per_launch * R
+    per_round = bench.phase3_relax_per_round(n, T)
+    phase4 = per_round * R
     phase123 = 0
     for r in range(R):
         m = min(T, n - r * T)
