@@ -469,11 +469,69 @@ def bench_fwd_bwd(torch, apsp, graphgen, args, dev):
             "note": "fwd includes the 64 MiB input restore copy"}
 
 
+def bench_sweep(torch, apsp, graphgen, args, dev, pair_rate=None):
+    """FP32 blocked FW over the sizes of the n sweep, with and without the path
+    matrix: solve time (device events around the call; the input is restored by
+    a device copy before each solve, outside the timed region), relax/s, the
+    fraction of the add+min peak (unit counts at the maximum SM clock, and the
+    measured instruction-pair rate), and the HBM rate of the algorithmic bytes
+    (D read + written and P written once per round: R (2s + 4) n^2 bytes) for the
+    whole solve and for phases 1-3 alone."""
+    facts = device_facts(torch)
+    peaks = measured_peaks()
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6777.0))
+    T = apsp.block_size(torch.float32)
+    peak_unit = alu_peak_relax_per_s(facts["sms"], max_mhz)
+    peak_meas = pair_rate * facts["sms"] * max_mhz * 1e6 if pair_rate else None
+    out = []
+    with ClockSampler(args.gpu_index) as clk:
+        for n in args.sweep:
+            W = graphgen.dense_graph_torch(n, 0.5, SEED, dtype=torch.float32, device=dev)
+            D = torch.empty_like(W)
+            P = torch.empty((n, n), dtype=torch.int32, device=dev)
+            R = (n + T - 1) // T
+            point = {"n": n}
+            for with_path in (True, False):
+                reps = 3 if n <= 8192 else 1
+                D.copy_(W)
+                apsp.apsp_fw_f32(D, P if with_path else None)  # warm-up
+                total = 0.0
+                apsp.profile_enable(True)
+                for _ in range(reps):
+                    D.copy_(W)
+                    total += time_events(torch, lambda: apsp.apsp_fw_f32(D, P if with_path else None))
+                prof = apsp.profile_collect()
+                apsp.profile_enable(False)
+                t = total / reps
+                bytes_round = (2 * 4 + (4 if with_path else 0)) * n * n
+                m = min(T, n)
+                p123_bytes = (2 * 4 + (4 if with_path else 0)) * (m * m + 2 * m * (n - m))  # per round
+                p123_ms = (prof["phase1_diag"][0] + prof["phase2_panels"][0]) / reps
+                point["with_path" if with_path else "without_path"] = {
+                    "ms": 1e3 * t, "relax_per_s": n ** 3 / t,
+                    "frac_of_unit_peak": n ** 3 / t / peak_unit,
+                    "frac_of_measured_pair_rate": (n ** 3 / t / peak_meas) if peak_meas else None,
+                    "phase_ms": {k: v[0] / reps for k, v in prof.items()},
+                    "hbm_gbs": R * bytes_round / t / 1e9, "hbm_frac": R * bytes_round / t / 1e9 / hbm,
+                    "phase1_3_hbm_gbs": (R * p123_bytes / (p123_ms / 1e3) / 1e9) if p123_ms > 0 else None}
+            out.append(point)
+            del W, D, P
+            torch.cuda.empty_cache()
+    return {"points": out, "clocks": clk.summary(), "dtype": "f32",
+            "peak_basis": f"{facts['sms']} SMs x 128 relax/clk/SM x {max_mhz:.0f} MHz; HBM {hbm:.0f} GB/s",
+            "note": "phases 1-3 run beside phase 4 (look-ahead stream), so their HBM rate is that of "
+                    "their own launches; n=4096 fits in L2"}
+
+
 def run_side_workload(args, torch, apsp, graphgen, dev):
     """--workload batched / fwd_bwd: that measurement alone (profiling runs)."""
     if args.workload == "batched":
         r = bench_batched(torch, apsp, graphgen, args, dev)
         line = {"metric": "batched graphs/s", "value": r["graphs_per_s"], "unit": "graphs/s", **r}
+    elif args.workload == "sweep":
+        r = bench_sweep(torch, apsp, graphgen, args, dev, apsp.measure_peak(4))
+        line = {"metric": "min-plus relaxations/s (FP32 n sweep)", "unit": UNIT, **r}
     else:
         r = bench_fwd_bwd(torch, apsp, graphgen, args, dev)
         line = {"metric": "forward+backward ms", "value": r["fwd_bwd_ms"], "unit": "ms",
@@ -580,6 +638,9 @@ def run_ours(args):
         line["batched"] = bench_batched(torch, apsp, graphgen, args, dev)
         torch.cuda.empty_cache()
         line["fwd_bwd"] = bench_fwd_bwd(torch, apsp, graphgen, args, dev)
+        torch.cuda.empty_cache()
+        if args.sweep:
+            line["sweep"] = bench_sweep(torch, apsp, graphgen, args, dev, rate_meas)
         # CPU baseline: the oracle as it stands, bounded prefix of the same graph
         rate, k, thr, tcpu = oracle_partial_rate(Wh.numpy(), args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -599,7 +660,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["single", "batched", "fwd_bwd"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "fwd_bwd", "sweep"], default="single",
                     help="single (the headline line) or one side measurement alone")
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32",
                     help="precision of the timed single-graph solve (the headline is f32)")
@@ -610,6 +671,9 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--gpu-index", default=None)
     ap.add_argument("--no-extras", action="store_true", help="only the FP32 timed steps")
+    ap.add_argument("--sweep", type=lambda x: [int(v) for v in x.split(",") if v], default=[4096, 8192, 32768, 65536],
+                    help="comma-separated FP32 sizes of the n sweep (empty: skip)")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_const", const=[])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

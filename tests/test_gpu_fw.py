@@ -189,7 +189,8 @@ def _dijkstra_check(D_dev, W_host, srcs):
 
 
 @pytest.mark.parametrize("n,dtype", [(16384, torch.float32), (16384, torch.float64),
-                                     (32768, torch.float32)])
+                                     (32768, torch.float32), (32768, torch.float64),
+                                     (65536, torch.float32)])
 def test_full_size_sampled_rows(n, dtype):
     """Full-size blocked FW (edge probability 0.5, integer weights): sampled
     rows against Dijkstra (exact) and sampled paths against the weights."""
