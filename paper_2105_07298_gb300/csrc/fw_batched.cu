@@ -75,14 +75,13 @@ union BatchedSmem {
 
 __device__ __forceinline__ void relax2_argmin(float &acc, int &idx, unsigned long long a,
                                               unsigned long long b, int k0) {
-  float c0, c1, m;
-  asm("{\n\t.reg .b64 t;\n\t"
-      "add.rn.f32x2 t, %3, %4;\n\t"
-      "mov.b64 {%0, %1}, t;\n\t"
-      "min.f32 %2, %5, %0, %1;\n\t}"
-      : "=f"(c0), "=f"(c1), "=f"(m)
+  float c0, m;
+  asm("{\n\t.reg .b64 t;\n\t.reg .f32 hi;\n\t"
+      "add.rn.f32x2 t, %2, %3;\n\t"
+      "mov.b64 {%0, hi}, t;\n\t"
+      "min.f32 %1, %4, %0, hi;\n\t}"
+      : "=f"(c0), "=f"(m)
       : "l"(a), "l"(b), "f"(acc));
-  (void)c1;
   if (m < acc) {
     idx = (c0 == m) ? k0 : k0 + 1;  // the lower k wins a tie inside the pair
     acc = m;

@@ -70,8 +70,12 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
 // outputs in registers; at step k the owners of row k and column k publish
 // them to shared memory (two alternating buffers, one barrier per step).
 // Step k never changes row or column k (D[k][k] = 0), so the published values
-// are the ones every thread must use.  Writes D (all valid outputs) and P
-// (where improved).
+// are the ones every thread must use.  k is walked as 32 kb + 2 kk + q with
+// kb and q unrolled, so the owners' register index is a constant; candidates
+// form in pairs (one add.rn.f32x2 for two adjacent columns), and the block-
+// local k of each output's last improvement is kept as a byte in registers.
+// Steps past the last valid vertex only meet +inf padding and change nothing.
+// Writes D (all valid outputs) and P (where improved).
 template <int TB>
 struct DiagSmemT {
   float row[2][TB];
@@ -83,9 +87,11 @@ template <int TM>
 __device__ __forceinline__ void diag_closure(float *__restrict__ D, int64_t ld,
                                              int32_t *__restrict__ P, int base, int m,
                                              DiagSmemT<16 * TM> &sm) {
+  static_assert(TM % 4 == 0, "columns are kept in pairs and path bytes in fours");
   const int ty = thread_ty(), tx = thread_tx();
   const float INF = inf<float>();
   float d[TM][TM];
+  unsigned pk[TM][TM / 4];  // byte cc % 4 of pk[rr][cc / 4]: local k, 0xFF none
 #pragma unroll
   for (int rr = 0; rr < TM; ++rr) {
     const int i = row_at(rr, ty);
@@ -94,36 +100,54 @@ __device__ __forceinline__ void diag_closure(float *__restrict__ D, int64_t ld,
       const int j = col_at(cc, tx);
       d[rr][cc] = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : INF;
     }
+#pragma unroll
+    for (int c4 = 0; c4 < TM / 4; ++c4) pk[rr][c4] = 0xFFFFFFFFu;
   }
-  for (int k = 0; k < m; ++k) {
-    const int buf = k & 1;
 #pragma unroll
-    for (int rr = 0; rr < TM; ++rr)
-      if (row_at(rr, ty) == k) {
+  for (int kb = 0; kb < TM / 2; ++kb) {
+#pragma unroll 1
+    for (int kk = 0; kk < 16; ++kk) {
 #pragma unroll
-        for (int cc = 0; cc < TM; ++cc) sm.row[buf][col_at(cc, tx)] = d[rr][cc];
-      }
+      for (int q = 0; q < 2; ++q) {
+        const int k = 32 * kb + 2 * kk + q;  // row_at / col_at index 2 kb + q of owner kk
+        if (ty == kk) {
 #pragma unroll
-    for (int cc = 0; cc < TM; ++cc)
-      if (col_at(cc, tx) == k) {
+          for (int cc = 0; cc < TM; cc += 2)
+            *reinterpret_cast<float2 *>(&sm.row[q][col_at(cc, tx)]) = make_float2(d[2 * kb + q][cc], d[2 * kb + q][cc + 1]);
+        }
+        if (tx == kk) {
 #pragma unroll
-        for (int rr = 0; rr < TM; ++rr) sm.col[buf][row_at(rr, ty)] = d[rr][cc];
-      }
-    __syncthreads();
-    float a[TM], b[TM];
+          for (int rr = 0; rr < TM; rr += 2)
+            *reinterpret_cast<float2 *>(&sm.col[q][row_at(rr, ty)]) = make_float2(d[rr][2 * kb + q], d[rr + 1][2 * kb + q]);
+        }
+        __syncthreads();
+        float a[TM];
+        unsigned long long b[TM / 2];
 #pragma unroll
-    for (int rr = 0; rr < TM; ++rr) a[rr] = sm.col[buf][row_at(rr, ty)];
+        for (int rr = 0; rr < TM; rr += 2) {
+          const float2 t = *reinterpret_cast<const float2 *>(&sm.col[q][row_at(rr, ty)]);
+          a[rr] = t.x;
+          a[rr + 1] = t.y;
+        }
 #pragma unroll
-    for (int cc = 0; cc < TM; ++cc) b[cc] = sm.row[buf][col_at(cc, tx)];
+        for (int cc = 0; cc < TM; cc += 2) b[cc / 2] = *reinterpret_cast<const unsigned long long *>(&sm.row[q][col_at(cc, tx)]);
 #pragma unroll
-    for (int rr = 0; rr < TM; ++rr) {
-      const int i = row_at(rr, ty);
+        for (int rr = 0; rr < TM; ++rr) {
+          const unsigned long long aa = pack2(a[rr], a[rr]);
 #pragma unroll
-      for (int cc = 0; cc < TM; ++cc) {
-        const float cand = __fadd_rn(a[rr], b[cc]);
-        if (cand < d[rr][cc]) {
-          d[rr][cc] = cand;
-          if (P) P[(int64_t)(base + i) * ld + base + col_at(cc, tx)] = base + k;
+          for (int c2 = 0; c2 < TM / 2; ++c2) {
+            const float2 cand = sum2(aa, b[c2]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int cc = 2 * c2 + h;
+              const float cv = h ? cand.y : cand.x;
+              if (cv < d[rr][cc]) {
+                d[rr][cc] = cv;
+                pk[rr][cc / 4] = __byte_perm(pk[rr][cc / 4], (unsigned)k,
+                                             0x3210 ^ ((0x3210 & (0xF << (4 * (cc & 3)))) ^ (4 << (4 * (cc & 3)))));
+              }
+            }
+          }
         }
       }
     }
@@ -134,7 +158,11 @@ __device__ __forceinline__ void diag_closure(float *__restrict__ D, int64_t ld,
 #pragma unroll
     for (int cc = 0; cc < TM; ++cc) {
       const int j = col_at(cc, tx);
-      if (i < m && j < m) D[(int64_t)(base + i) * ld + base + j] = d[rr][cc];
+      if (i < m && j < m) {
+        D[(int64_t)(base + i) * ld + base + j] = d[rr][cc];
+        const unsigned kl = (pk[rr][cc / 4] >> (8 * (cc & 3))) & 0xFFu;
+        if (P && kl != 0xFFu) P[(int64_t)(base + i) * ld + base + j] = base + (int)kl;
+      }
     }
   }
 }
