@@ -205,7 +205,10 @@ struct Smem {
 };
 }  // namespace k3
 
-__global__ void __launch_bounds__(mp32::THREADS, 3)
+#ifndef APSP_K3_MIN_BLOCKS
+#define APSP_K3_MIN_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
     fw_phase3_minplus_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
                           int R, int vec_ok, Panels pan, int set) {
   using namespace k3;
