@@ -45,6 +45,11 @@ constexpr int THREADS = 256;  // product: 8 warps, 4 x 8 outputs per thread, 128
 constexpr int H = T / 2;      // output columns per CTA (one half of a block)
 constexpr int KS = 32, KP = 16, STAGES = 2;
 constexpr uint32_t SLAB_BYTES = KP * H * 8;  // one half of one paired array, one slab
+#ifndef APSP_F64_DENSE_MIN
+#define APSP_F64_DENSE_MIN 40
+#endif
+// Quick improvements (of 512) above which an 8-row group takes recovery pass 2a.
+constexpr int kDenseMin64 = APSP_F64_DENSE_MIN;
 
 // One operand block packed for the product kernel.  For an A operand
 // (A[i][k]): lo[i/64][kp][i%64] = (rd A[i][2kp], rd A[i][2kp+1]), hi likewise
@@ -108,6 +113,23 @@ __device__ __forceinline__ unsigned long long dkey_bits(long long k) {
 
 __device__ __forceinline__ unsigned long long packf2(float lo, float hi) {
   return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+
+// The two bound sums of relax2_rm / relax2_rp, unfolded (same rounding).
+__device__ __forceinline__ float2 sum2_rm(unsigned long long a, unsigned long long b) {
+  unsigned long long t;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(b));
+  return make_float2(__uint_as_float((unsigned)t), __uint_as_float((unsigned)(t >> 32)));
+}
+__device__ __forceinline__ float2 sum2_rp(unsigned long long a, unsigned long long b) {
+  unsigned long long t;
+  asm("add.rp.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(b));
+  return make_float2(__uint_as_float((unsigned)t), __uint_as_float((unsigned)(t >> 32)));
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
 __device__ __forceinline__ void relax2_rm(float &acc, unsigned long long a, unsigned long long b) {
@@ -423,11 +445,99 @@ __global__ void __launch_bounds__(THREADS, 2)
         slow |= 1u << (2 * t + q);
       }
     }
-  // Pass 2: every flagged output, the warp's flagged outputs walked as one
-  // stream two at a time (the bound rows of both load together); lane l
+  // Pass 2a (path matrix only): each 8-row group of the warp with many quick
+  // improvements (the early rounds) recovers P lane-parallel.  For a quick
+  // output the exact minimum is the float X = min lo, so the k sought is the
+  // first one whose exact sum is X; such a k has lo_k = X.  Lane l scans the
+  // lower-bound pairs of its two columns over all k (B pairs coalesced, A
+  // pairs broadcast, add.rm.f32x2 as in the main loop), folds every 8 k into
+  // one minimum, and keeps the lowest 8-k chunk whose minimum is X.  Inside
+  // that chunk the first k with lo_k = X and an exact sum of X is taken (the
+  // sum is exact when lo_k = up_k, else one FP64 add decides).  An output
+  // whose chunk holds no such k (possible only with real weights) is left to
+  // pass 2b.
+  const int jb0 = hJ * H;  // column offset of this half inside the B pack
+  unsigned quick_left = P ? quick : 0u;
+  if (P) {
+    const unsigned long long *pbl = &B->lo[hJ][0][j0], *pbh = &B->hi[hJ][0][j0];
+#pragma unroll 1
+    for (int G = 0; G < 2; ++G) {
+      const unsigned gm = 0xFFFFu << (16 * G);
+      if ((int)__reduce_add_sync(kFullMask, (unsigned)__popc(quick & gm)) < kDenseMin64) continue;
+      const int tg0 = 8 * G;
+      float g[8][2];
+      unsigned hit[8];  // bit c (+16 for column j0 + 1): chunk c's minimum lo equals X
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const float2 x = *reinterpret_cast<const float2 *>(&Lo[(i0 + tg0 + t) * H + j0]);
+        g[t][0] = x.x;
+        g[t][1] = x.y;
+        hit[t] = 0u;
+      }
+#pragma unroll 1
+      for (int c = T / 8 - 1; c >= 0; --c) {
+        ulonglong2 b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = __ldg(reinterpret_cast<const ulonglong2 *>(pbl + (4 * c + q) * H));
+        const unsigned bit = 1u << c;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int i = i0 + tg0 + t;
+          const unsigned long long *pal = &A->lo[i >> 6][0][i & 63];
+          unsigned long long a[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a[q] = __ldg(pal + (4 * c + q) * H);
+#pragma unroll
+          for (int q2 = 0; q2 < 2; ++q2) {
+            const float2 s0 = sum2_rm(a[0], q2 ? b[0].y : b[0].x), s1 = sum2_rm(a[1], q2 ? b[1].y : b[1].x);
+            const float2 s2 = sum2_rm(a[2], q2 ? b[2].y : b[2].x), s3 = sum2_rm(a[3], q2 ? b[3].y : b[3].x);
+            float m = min3f(s0.x, s0.y, s1.x);
+            m = min3f(m, s1.y, s2.x);
+            m = min3f(m, s2.y, s3.x);
+            m = fminf(m, s3.y);
+            if (m == g[t][q2]) hit[t] |= bit << (16 * q2);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = i0 + tg0 + t;
+        const unsigned long long *pal = &A->lo[i >> 6][0][i & 63], *pah = &A->hi[i >> 6][0][i & 63];
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+          const unsigned bitq = 1u << (2 * (tg0 + t) + q2);
+          if (!(quick & bitq)) continue;
+          const unsigned cm = (hit[t] >> (16 * q2)) & 0xFFFFu;  // not empty: X is some lo
+          const int c = __ffs(cm) - 1;
+          const float X = g[t][q2];
+          int kf = -1;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int kp = 4 * c + q;
+            const float2 l = sum2_rm(__ldg(pal + kp * H), __ldg(pbl + kp * H + q2));
+            const float2 u = sum2_rp(__ldg(pah + kp * H), __ldg(pbh + kp * H + q2));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int k = 2 * kp + h;
+              if (kf < 0 && (h ? l.y : l.x) == X &&
+                  ((h ? u.y : u.x) == X ||
+                   __dadd_rn(A->r64[i][k], B->r64[jb0 + j0 + q2][k]) == __longlong_as_double((long long)f32_to_f64_bits(X))))
+                kf = k;
+            }
+          }
+          if (kf >= 0) {
+            P[(int64_t)(baseI + i) * ld + baseJ + j0 + q2] = baseK + kf;
+            quick_left &= ~bitq;
+          }
+        }
+      }
+    }
+  }
+  // Pass 2b: every remaining flagged output, the warp's flagged outputs walked
+  // as one stream two at a time (the bound rows of both load together); lane l
   // tests k = 4l..4l+3.  quick: recover the first k whose exact sum is X;
   // slow: exact FP64 minimum over the candidates with lo <= min(up, ru(old)).
-  const unsigned todo = quick | slow;
+  const unsigned todo = quick_left | slow;
   unsigned wf = __reduce_or_sync(kFullMask, todo);
   unsigned bal = 0u;
   int pos = 0;
@@ -445,7 +555,6 @@ __global__ void __launch_bounds__(THREADS, 2)
     is_slow = (__shfl_sync(kFullMask, slow, src) >> pos) & 1u;
     return true;
   };
-  const int jb0 = hJ * H;  // column offset of this half inside the B pack
 #pragma unroll 1
   for (;;) {
     int t[2], sj[2];
