@@ -302,19 +302,43 @@ __device__ __forceinline__ void issue_slab(ProdSmem &sm, int st, const Pack *A, 
   bulk_g2s(&sm.Bhi[st][0][0], &B->hi[hJ][s * KP][0], SLAB_BYTES, &sm.bar[st]);
 }
 
+// Block sets of one phase-4 launch (MODE 0; grid: 2 CTAs per block).
+constexpr int kSetAll = 0;   // all (R-1)^2 blocks off row/column r
+constexpr int kSetNext = 1;  // the 2R-3 blocks in row r+1 or column r+1
+constexpr int kSetRest = 2;  // the (R-2)^2 blocks off rows/columns r and r+1
+
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 2)
     fw64_product(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R,
-                 Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB) {
+                 Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB, int set) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   ProdSmem &sm = *reinterpret_cast<ProdSmem *>(smem_raw);
   const int tile = blockIdx.x >> 1, hJ = blockIdx.x & 1;
   int I, J;
   if (MODE == 0) {
-    I = tile / (R - 1);
-    J = tile % (R - 1);
-    I += (I >= r);
-    J += (J >= r);
+    if (set == kSetAll) {
+      I = tile / (R - 1);
+      J = tile % (R - 1);
+      I += (I >= r);
+      J += (J >= r);
+    } else if (set == kSetNext) {  // row r+1, then column r+1: the next round's K1/K2 input
+      if (tile < R - 1) {
+        I = r + 1;
+        J = tile + (tile >= r);
+      } else {
+        I = tile - (R - 1);
+        I += (I >= r);
+        I += (I >= r + 1);
+        J = r + 1;
+      }
+    } else {  // the rest: rows and columns other than r and r+1
+      I = tile / (R - 2);
+      J = tile % (R - 2);
+      I += (I >= r);
+      I += (I >= r + 1);
+      J += (J >= r);
+      J += (J >= r + 1);
+    }
   } else if (MODE == 1) {
     I = r;
     J = tile + (tile >= r);
@@ -692,34 +716,80 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
   if ((st = ensure_smem(fw64_product<0>, smemp, g_smem_p0))) return st;
   if ((st = ensure_smem(fw64_product<1>, smemp, g_smem_p1))) return st;
   if ((st = ensure_smem(fw64_product<2>, smemp, g_smem_p2))) return st;
+  // Operand packs: two sets by round parity (so that phases 1-3 of round
+  // r+1 can pack while phase 4 of round r still reads), each R column-panel
+  // packs, R row-panel packs and the diagonal block as A and as B operand.
+  struct PackSet {
+    Pack *A, *B, *dA, *dB;
+  } ps[2]{};
   char *scratch = nullptr;
-  Pack *packA = nullptr, *packB = nullptr, *diagA = nullptr, *diagB = nullptr;
   if (R > 1) {
-    if (cudaMallocAsync((void **)&scratch, sizeof(Pack) * (2 * (size_t)R + 2), s) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&scratch, sizeof(Pack) * 2 * (2 * (size_t)R + 2), s) != cudaSuccess) {
       cudaGetLastError();
       return APSP_ENOMEM;
     }
-    packA = reinterpret_cast<Pack *>(scratch);
-    packB = packA + R;
-    diagA = packB + R;
-    diagB = diagA + 1;
+    for (int q = 0; q < 2; ++q) {
+      Pack *base = reinterpret_cast<Pack *>(scratch) + (size_t)q * (2 * R + 2);
+      ps[q] = {base, base + R, base + 2 * R, base + 2 * R + 1};
+    }
   }
-  for (int r = 0; r < R; ++r) {
+  auto diag_and_panels = [&](int r, cudaStream_t stm) {
+    const PackSet &p = ps[r & 1];
     {
-      PhaseScope ps(1, s);
-      fw64_diag<<<1, K1_THREADS, smem1, s>>>(D, ld, P, n, r, diagA, diagB);
+      PhaseScope sc(1, stm);
+      fw64_diag<<<1, K1_THREADS, smem1, stm>>>(D, ld, P, n, r, p.dA, p.dB);
     }
     if (R > 1) {
-      {
-        PhaseScope ps(2, s);
-        fw64_pack_panels<<<2 * (R - 1), K2A_THREADS, smem2a, s>>>(D, ld, n, r, R, packA, packB);
-        fw64_product<1><<<2 * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
-        fw64_product<2><<<2 * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB, diagA, diagB);
-      }
-      PhaseScope ps(3, s);
-      fw64_product<0><<<2 * (R - 1) * (R - 1), THREADS, smemp, s>>>(D, ld, P, n, r, R, packA, packB,
-                                                                     diagA, diagB);
+      PhaseScope sc(2, stm);
+      fw64_pack_panels<<<2 * (R - 1), K2A_THREADS, smem2a, stm>>>(D, ld, n, r, R, p.A, p.B);
+      fw64_product<1><<<2 * (R - 1), THREADS, smemp, stm>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, 0);
+      fw64_product<2><<<2 * (R - 1), THREADS, smemp, stm>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, 0);
     }
+  };
+  auto phase4 = [&](int r, int set, int blocks) {
+    if (blocks <= 0) return;
+    const PackSet &p = ps[r & 1];
+    PhaseScope sc(3, s);
+    fw64_product<0><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, set);
+  };
+  // Look-ahead as in the FP32 path: phase 4 of round r updates row and
+  // column r+1 first; phases 1-3 of round r+1 then run on a second stream of
+  // higher priority beside the rest of phase 4 (disjoint blocks, the other
+  // pack set).
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_next = nullptr, ev_panels = nullptr;
+  if (R > 2) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_next, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_panels, cudaEventDisableTiming) != cudaSuccess) {
+      if (s2) cudaStreamDestroy(s2);
+      if (ev_next) cudaEventDestroy(ev_next);
+      if (scratch) cudaFreeAsync(scratch, s);
+      cudaGetLastError();
+      return APSP_ECUDA;
+    }
+  }
+  diag_and_panels(0, s);
+  for (int r = 0; R > 1 && r < R; ++r) {
+    if (r + 1 < R && s2) {
+      phase4(r, kSetNext, 2 * R - 3);
+      cudaEventRecord(ev_next, s);
+      cudaStreamWaitEvent(s2, ev_next, 0);
+      diag_and_panels(r + 1, s2);
+      cudaEventRecord(ev_panels, s2);
+      phase4(r, kSetRest, (R - 2) * (R - 2));
+      cudaStreamWaitEvent(s, ev_panels, 0);
+    } else {
+      phase4(r, kSetAll, (R - 1) * (R - 1));
+      if (r + 1 < R) diag_and_panels(r + 1, s);
+    }
+  }
+  if (s2) {
+    cudaStreamDestroy(s2);
+    cudaEventDestroy(ev_next);
+    cudaEventDestroy(ev_panels);
   }
   cudaError_t e = cudaGetLastError();
   if (scratch) {
