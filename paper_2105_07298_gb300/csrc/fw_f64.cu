@@ -557,11 +557,72 @@ __global__ void __launch_bounds__(THREADS, 2)
       }
     }
   }
-  // Pass 2b: every remaining flagged output, the warp's flagged outputs walked
-  // as one stream two at a time (the bound rows of both load together); lane l
-  // tests k = 4l..4l+3.  quick: recover the first k whose exact sum is X;
-  // slow: exact FP64 minimum over the candidates with lo <= min(up, ru(old)).
-  const unsigned todo = quick_left | slow;
+  // Pass 2b (path matrix only): the remaining quick improvements, walked as
+  // one stream four at a time; lane l tests k = 4l..4l+3.  Only a k with
+  // lo_k = X can carry the exact sum X, so the lower-bound rows load first
+  // (two float4 per output) and a hit fetches its upper bounds (and, if they
+  // differ, its FP64 operands) alone.  The candidate that attains min up has
+  // lo = up = X, so every quick output has a hit.
+  {
+    unsigned wq = __reduce_or_sync(kFullMask, quick_left), balq = 0u;
+    int posq = 0;
+    auto nextq = [&](int &t, int &sj) -> bool {  // warp-uniform
+      while (!balq) {
+        if (!wq) return false;
+        posq = __ffs(wq) - 1;
+        wq &= wq - 1;
+        balq = __ballot_sync(kFullMask, (quick_left >> posq) & 1u);
+      }
+      const int src = __ffs(balq) - 1;
+      balq &= balq - 1;
+      t = posq >> 1;
+      sj = 2 * src + (posq & 1);
+      return true;
+    };
+#pragma unroll 1
+    for (;;) {
+      int t[4], sj[4];
+      bool v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = nextq(t[u], sj[u]);
+      if (!v[0]) break;
+      float4 al[4], bl[4];
+      float X[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!v[u]) continue;
+        const int i = i0 + t[u];
+        al[u] = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
+        bl[u] = reinterpret_cast<const float4 *>(&B->rlo[jb0 + sj[u]][0])[lane];
+        X[u] = Lo[i * H + sj[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!v[u]) continue;
+        const int i = i0 + t[u], jb = jb0 + sj[u];
+        const float la[4] = {al[u].x, al[u].y, al[u].z, al[u].w};
+        const float lb[4] = {bl[u].x, bl[u].y, bl[u].z, bl[u].w};
+        unsigned h = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int k = 4 * lane + q;
+          if (__fadd_rd(la[q], lb[q]) == X[u] &&
+              (__fadd_ru(A->rhi[i][k], B->rhi[jb][k]) == X[u] ||
+               __dadd_rn(A->r64[i][k], B->r64[jb][k]) == __longlong_as_double((long long)f32_to_f64_bits(X[u]))))
+            h |= 1u << q;
+        }
+        const unsigned hb = __ballot_sync(kFullMask, h != 0u);
+        const int L = __ffs(hb) - 1;
+        const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
+        if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj[u]] = baseK + 4 * L + (__ffs(hL) - 1);
+      }
+    }
+  }
+  // Pass 2c: the slow outputs (bounds that do not decide; real weights), the
+  // warp's flagged outputs walked as one stream two at a time (the bound rows
+  // of both load together); lane l tests k = 4l..4l+3: exact FP64 minimum over
+  // the candidates with lo <= min(up, ru(old)), first k on ties.
+  const unsigned todo = slow;
   unsigned wf = __reduce_or_sync(kFullMask, todo);
   unsigned bal = 0u;
   int pos = 0;
