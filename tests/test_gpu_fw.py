@@ -44,7 +44,7 @@ def _sample_pairs(n, count, seed):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-@pytest.mark.parametrize("n", [1, 2, 3, 31, 64, 65, 127, 128, 129, 200, 255, 257, 300])
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 64, 65, 127, 128, 129, 200, 255, 257, 300, 384, 385, 513])
 def test_integer_weights_bit_exact(n, dtype):
     W = graphgen.dense_graph(n, 0.3, 1000 + n, dtype=dtype)
     D, P, _ = _run(W, dtype)
@@ -53,7 +53,7 @@ def test_integer_weights_bit_exact(n, dtype):
     assert oracle.check_paths(W, D, P) == 0
 
 
-@pytest.mark.parametrize("n", [70, 200, 333])
+@pytest.mark.parametrize("n", [70, 200, 333, 513])
 def test_real_weights_f32_match_blocked_oracle_bitwise(n):
     """FP32 follows the paper's four phases exactly: same sums, same order of k."""
     W = graphgen.dense_graph(n, 0.4, 77 + n, weights="real", lo=0.5, hi=2.0, dtype=np.float32)
@@ -69,7 +69,7 @@ def test_real_weights_f32_match_blocked_oracle_bitwise(n):
     assert oracle.check_paths(W, D, P, rtol=1e-5) == 0
 
 
-@pytest.mark.parametrize("n,p", [(70, 0.4), (200, 0.4), (333, 0.4), (300, 0.05)])
+@pytest.mark.parametrize("n,p", [(70, 0.4), (200, 0.4), (333, 0.4), (300, 0.05), (513, 0.4)])
 def test_real_weights_f64_within_1e12(n, p):
     """FP64 (phases 2/3 through the closed diagonal block): within 1e-12 relative
     of the exact FP64 distances; phase 1 and 4 candidate sums are IEEE FP64."""
