@@ -8,13 +8,16 @@
 //  * each FP64 operand x is held as the float interval [rd(x), ru(x)]
 //    (largest float <= x, smallest float >= x);
 //  * a candidate a + b then lies in [lo, up] with lo = rd(rd(a) + rd(b)) and
-//    up = ru(ru(a) + ru(b)) (packed add.rm.f32x2 / add.rp.f32x2), and so does
-//    its FP64 rounding fl(a + b), since rounding is monotone;
-//  * the min-plus product keeps min lo and min up per output.  If
-//    min lo >= ru(old) nothing can beat the old value; if min lo == min up
-//    the exact FP64 minimum IS that float (integer-valued weights always land
-//    here); otherwise the few candidates with lo <= min(min up, ru(old)) are
-//    evaluated with a real FP64 add, warp-cooperatively.
+//    up = ru(ru(a) + ru(b)) (add.rm / add.rp), and so does its FP64 rounding
+//    fl(a + b), since rounding is monotone;
+//  * the min-plus product runs on the lower bounds alone (one packed
+//    add.rm.f32x2 and one three-input min per two candidates, as the FP32
+//    kernel) and keeps X = min lo per output.  If X >= ru(old) nothing can
+//    beat the old value.  Otherwise the exact FP64 minimum is X when some
+//    candidate with lo = X has an exact sum X (its upper bound is X, or one
+//    FP64 add says so; integer-valued weights always land here), and the
+//    first such k is the path entry; if none has, the candidates with
+//    lo <= min(ru(old), their up) are evaluated with a real FP64 add.
 //
 // Schedule per round r (TB = 128), the blocked FW of §2.2:
 //  K1  fw64_diag         phase 1: Algorithm 1 on block (r,r), k sequential,
@@ -270,16 +273,23 @@ __global__ void __launch_bounds__(K2A_THREADS)
 }
 
 // ---------------------------------------------------------------- products
-// A CTA computes one 128 x 64 half of an output block (two CTAs per block, two
-// CTAs per SM):
-// MODE 0: phase 4, C = (I,J), A = packA[I], B = packB[J] (grid 2 (R-1)^2)
+// A CTA computes one 128 x 64 half of an output block (two CTAs per block,
+// three CTAs per SM):
+// MODE 0: phase 4, C = (I,J), A = packA[I], B = packB[J] (grid: per block set)
 // MODE 1: phase 2, C = (r,J), A = diagA,    B = packB[J] (grid 2 (R-1)), re-packs C into packB[J]
 // MODE 2: phase 3, C = (I,r), A = packA[I], B = diagB    (grid 2 (R-1)), re-packs C into packA[I]
+//
+// Only the lower bounds enter the main loop.  X = min_k lo_k is a lower bound
+// of the exact FP64 minimum s* (lo_k <= s_k for every k), so X >= ru(old)
+// means no improvement.  Otherwise s* = X exactly when some k with lo_k = X
+// has an exact sum of X (its upper bound is X too, or one FP64 add says so),
+// and the first such k is the path entry; if none has, s* > X and the exact
+// minimum is taken over the candidates with lo_k <= min(ru(old),
+// min{up_k : lo_k = X}) (an upper bound of s*).  With integer weights every
+// sum is exact and the first case always holds.
 struct ProdSmem {
   unsigned long long Alo[STAGES][2][KP][H];  // both row halves of the A slab
-  unsigned long long Ahi[STAGES][2][KP][H];
   unsigned long long Blo[STAGES][KP][H];     // this CTA's column half of the B slab
-  unsigned long long Bhi[STAGES][KP][H];
   uint64_t bar[STAGES];
 };
 
@@ -293,13 +303,9 @@ __device__ __forceinline__ int col8(int c, int tx) { return (c >> 1) * 16 + tx *
 
 __device__ __forceinline__ void issue_slab(ProdSmem &sm, int st, const Pack *A, const Pack *B, int hJ,
                                            int s) {
-  mbar_expect_tx(&sm.bar[st], 6 * SLAB_BYTES);
-  for (int h = 0; h < 2; ++h) {
-    bulk_g2s(&sm.Alo[st][h][0][0], &A->lo[h][s * KP][0], SLAB_BYTES, &sm.bar[st]);
-    bulk_g2s(&sm.Ahi[st][h][0][0], &A->hi[h][s * KP][0], SLAB_BYTES, &sm.bar[st]);
-  }
+  mbar_expect_tx(&sm.bar[st], 3 * SLAB_BYTES);
+  for (int h = 0; h < 2; ++h) bulk_g2s(&sm.Alo[st][h][0][0], &A->lo[h][s * KP][0], SLAB_BYTES, &sm.bar[st]);
   bulk_g2s(&sm.Blo[st][0][0], &B->lo[hJ][s * KP][0], SLAB_BYTES, &sm.bar[st]);
-  bulk_g2s(&sm.Bhi[st][0][0], &B->hi[hJ][s * KP][0], SLAB_BYTES, &sm.bar[st]);
 }
 
 // Block sets of one phase-4 launch (MODE 0; grid: 2 CTAs per block).
@@ -307,8 +313,10 @@ constexpr int kSetAll = 0;   // all (R-1)^2 blocks off row/column r
 constexpr int kSetNext = 1;  // the 2R-3 blocks in row r+1 or column r+1
 constexpr int kSetRest = 2;  // the (R-2)^2 blocks off rows/columns r and r+1
 
+__device__ __forceinline__ double f32_as_f64(float x) { return __longlong_as_double((long long)f32_to_f64_bits(x)); }
+
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, 2)
+__global__ void __launch_bounds__(THREADS, 3)
     fw64_product(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R,
                  Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB, int set) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -363,11 +371,11 @@ __global__ void __launch_bounds__(THREADS, 2)
   }
   __syncthreads();
 
-  float lo[4][8], up[4][8];
+  float lo[4][8];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) lo[a][c] = up[a][c] = FINF;
+    for (int c = 0; c < 8; ++c) lo[a][c] = FINF;
 
   for (int s = 0; s < nslab; ++s) {
     const int st = s % STAGES;
@@ -380,12 +388,11 @@ __global__ void __launch_bounds__(THREADS, 2)
       }
       return;
     }
-    // Hand-pipelined operand loads: the hi operands of k-pair kp load while
-    // its lo products run, and the lo operands of kp+1 while its hi products
-    // run (two named operand sets; the compiler's unrolling would spill).
-    unsigned long long al[4], bl[8], ah[4], bh[8];
-    auto load_set = [&](int kp, const unsigned long long (*As)[KP][H], const unsigned long long (*Bs)[H],
-                        unsigned long long (&a)[4], unsigned long long (&b)[8]) {
+    const unsigned long long(*As)[KP][H] = sm.Alo[st];
+    const unsigned long long(*Bs)[H] = sm.Blo[st];
+#pragma unroll 1
+    for (int kp = 0; kp < KP; ++kp) {
+      unsigned long long a[4], b[8];
 #pragma unroll
       for (int rr = 0; rr < 4; rr += 2) {
         const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&As[rr >> 1][kp][ty * 2]);
@@ -398,20 +405,10 @@ __global__ void __launch_bounds__(THREADS, 2)
         b[cc] = t.x;
         b[cc + 1] = t.y;
       }
-    };
-    load_set(0, sm.Alo[st], sm.Blo[st], al, bl);
-#pragma unroll 1
-    for (int kp = 0; kp < KP; ++kp) {
-      load_set(kp, sm.Ahi[st], sm.Bhi[st], ah, bh);
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) relax2_rm(lo[rr][cc], al[rr], bl[cc]);
-      if (kp + 1 < KP) load_set(kp + 1, sm.Alo[st], sm.Blo[st], al, bl);
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < 8; ++cc) relax2_rp(up[rr][cc], ah[rr], bh[cc]);
+        for (int cc = 0; cc < 8; ++cc) relax2_rm(lo[rr][cc], a[rr], b[cc]);
     }
     __syncthreads();
     if (tid == 0 && s + STAGES < nslab) {
@@ -420,74 +417,51 @@ __global__ void __launch_bounds__(THREADS, 2)
     }
   }
 
-  // Epilogue.  The ring is free: min-lo and min-up go to shared memory, then
-  // each warp owns 16 whole rows (lane l: columns 2l, 2l+1 of the half).
-  // Per output:
-  //   X = min lo >= ru(old):          nothing can beat old;
-  //   X == min up (exact min = X):    improved iff X < old; P recovered below;
-  //   otherwise ("slow"):             exact FP64 resolution below.
-  // D may be written at once: the recovery reads only the packed operands.
+  // Epilogue.  The ring is free: X = min lo goes to shared memory, then each
+  // warp owns 16 whole rows (lane l: columns 2l, 2l+1 of the half).
   float *Lo = reinterpret_cast<float *>(smem_raw);  // [T][H]
-  float *Up = Lo + T * H;                           // [T][H]
   __syncthreads();
 #pragma unroll
   for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-    for (int cc = 0; cc < 8; cc += 2) {
-      const int i = row4(rr, ty), j = col8(cc, tx);
-      *reinterpret_cast<float2 *>(&Lo[i * H + j]) = make_float2(lo[rr][cc], lo[rr][cc + 1]);
-      *reinterpret_cast<float2 *>(&Up[i * H + j]) = make_float2(up[rr][cc], up[rr][cc + 1]);
-    }
+    for (int cc = 0; cc < 8; cc += 2)
+      *reinterpret_cast<float2 *>(&Lo[row4(rr, ty) * H + col8(cc, tx)]) = make_float2(lo[rr][cc], lo[rr][cc + 1]);
   __syncthreads();
-  const int j0 = 2 * lane, i0 = w * 16;
-  // Pass 1 (unrolled): the warp's 16 x 64 old values are loaded before any is
-  // used (one memory round trip); outputs are classified and quick
-  // improvements written.  Bit 2t + q of quick/slow: row i0 + t, column j0 + q.
-  double o[16][2];
+  const int j0 = 2 * lane, i0 = w * 16, jb0 = hJ * H;
+  // Pass 1: outputs that may improve (X < ru(old)).  Bit 2t + q of `pot`:
+  // row i0 + t, column j0 + q.  Old values load eight rows at a time.
+  unsigned pot = 0u;
 #pragma unroll
-  for (int t = 0; t < 16; ++t)
+  for (int t8 = 0; t8 < 16; t8 += 8) {
+    double o[8][2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
-      o[t][q] = (i0 + t < mI && j0 + q < mJ) ? D[(int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q]
-                                             : inf<double>();
-  unsigned quick = 0u, slow = 0u;
+    for (int t = 0; t < 8; ++t)
 #pragma unroll
-  for (int t = 0; t < 16; ++t)
+      for (int q = 0; q < 2; ++q)
+        o[t][q] = (i0 + t8 + t < mI && j0 + q < mJ) ? D[(int64_t)(baseI + i0 + t8 + t) * ld + baseJ + j0 + q]
+                                                     : inf<double>();
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int i = i0 + t, j = j0 + q;
-      if (i >= mI || j >= mJ) continue;
-      const float X = Lo[i * H + j];
-      if (!(X < f64_up(o[t][q]))) continue;
-      if (X == Up[i * H + j]) {
-        const unsigned long long xb = f32_to_f64_bits(X);
-        if (dkey(xb) < dkey((unsigned long long)__double_as_longlong(o[t][q]))) {
-          D[(int64_t)(baseI + i) * ld + baseJ + j] = __longlong_as_double((long long)xb);
-          quick |= 1u << (2 * t + q);
-        }
-      } else {
-        slow |= 1u << (2 * t + q);
+    for (int t = 0; t < 8; ++t) {
+      const float2 x = *reinterpret_cast<const float2 *>(&Lo[(i0 + t8 + t) * H + j0]);
+      if (i0 + t8 + t < mI) {
+        if (j0 < mJ && x.x < f64_up(o[t][0])) pot |= 1u << (2 * (t8 + t));
+        if (j0 + 1 < mJ && x.y < f64_up(o[t][1])) pot |= 2u << (2 * (t8 + t));
       }
     }
-  // Pass 2a (path matrix only): each 8-row group of the warp with many quick
-  // improvements (the early rounds) recovers P lane-parallel.  For a quick
-  // output the exact minimum is the float X = min lo, so the k sought is the
-  // first one whose exact sum is X; such a k has lo_k = X.  Lane l scans the
-  // lower-bound pairs of its two columns over all k (B pairs coalesced, A
-  // pairs broadcast, add.rm.f32x2 as in the main loop), folds every 8 k into
-  // one minimum, and keeps the lowest 8-k chunk whose minimum is X.  Inside
-  // that chunk the first k with lo_k = X and an exact sum of X is taken (the
-  // sum is exact when lo_k = up_k, else one FP64 add decides).  An output
-  // whose chunk holds no such k (possible only with real weights) is left to
-  // pass 2b.
-  const int jb0 = hJ * H;  // column offset of this half inside the B pack
-  unsigned quick_left = P ? quick : 0u;
-  if (P) {
-    const unsigned long long *pbl = &B->lo[hJ][0][j0], *pbh = &B->hi[hJ][0][j0];
+  }
+  // Pass 2a: each 8-row group of the warp with many candidates (the early
+  // rounds) is scanned lane-parallel: lane l walks the lower-bound pairs of
+  // its two columns over all k (B pairs coalesced, A pairs broadcast,
+  // add.rm.f32x2 as in the main loop), folds every 8 k into one minimum, and
+  // keeps the lowest 8-k chunk whose minimum is X.  Inside that chunk the
+  // first k with lo_k = X and an exact sum X settles the output (D where X <
+  // old, and P); an output without one there is left to pass 2b.
+  {
+    const unsigned long long *pbl = &B->lo[hJ][0][j0];
 #pragma unroll 1
     for (int G = 0; G < 2; ++G) {
       const unsigned gm = 0xFFFFu << (16 * G);
-      if ((int)__reduce_add_sync(kFullMask, (unsigned)__popc(quick & gm)) < kDenseMin64) continue;
+      if ((int)__reduce_add_sync(kFullMask, (unsigned)__popc(pot & gm)) < kDenseMin64) continue;
       const int tg0 = 8 * G;
       float g[8][2];
       unsigned hit[8];  // bit c (+16 for column j0 + 1): chunk c's minimum lo equals X
@@ -526,161 +500,132 @@ __global__ void __launch_bounds__(THREADS, 2)
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int i = i0 + tg0 + t;
-        const unsigned long long *pal = &A->lo[i >> 6][0][i & 63], *pah = &A->hi[i >> 6][0][i & 63];
+        const unsigned long long *pal = &A->lo[i >> 6][0][i & 63];
 #pragma unroll
         for (int q2 = 0; q2 < 2; ++q2) {
           const unsigned bitq = 1u << (2 * (tg0 + t) + q2);
-          if (!(quick & bitq)) continue;
+          if (!(pot & bitq)) continue;
           const unsigned cm = (hit[t] >> (16 * q2)) & 0xFFFFu;  // not empty: X is some lo
           const int c = __ffs(cm) - 1;
           const float X = g[t][q2];
-          int kf = -1;
+          const int jb = jb0 + j0 + q2;
+          // the chunk's eight lower-bound sums; upper bounds (and FP64 sums)
+          // only for a k whose lower bound is X, in ascending k
+          unsigned eq = 0u;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int kp = 4 * c + q;
-            const float2 l = sum2_rm(__ldg(pal + kp * H), __ldg(pbl + kp * H + q2));
-            const float2 u = sum2_rp(__ldg(pah + kp * H), __ldg(pbh + kp * H + q2));
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int k = 2 * kp + h;
-              if (kf < 0 && (h ? l.y : l.x) == X &&
-                  ((h ? u.y : u.x) == X ||
-                   __dadd_rn(A->r64[i][k], B->r64[jb0 + j0 + q2][k]) == __longlong_as_double((long long)f32_to_f64_bits(X))))
-                kf = k;
+            const float2 l = sum2_rm(__ldg(pal + (4 * c + q) * H), __ldg(pbl + (4 * c + q) * H + q2));
+            eq |= (l.x == X ? 1u : 0u) << (2 * q);
+            eq |= (l.y == X ? 1u : 0u) << (2 * q + 1);
+          }
+          int kf = -1;
+#pragma unroll 1
+          while (eq) {
+            const int k = 8 * c + __ffs(eq) - 1;
+            eq &= eq - 1;
+            if (__fadd_ru(A->rhi[i][k], B->rhi[jb][k]) == X ||
+                __dadd_rn(A->r64[i][k], B->r64[jb][k]) == f32_as_f64(X)) {
+              kf = k;
+              break;
             }
           }
-          if (kf >= 0) {
-            P[(int64_t)(baseI + i) * ld + baseJ + j0 + q2] = baseK + kf;
-            quick_left &= ~bitq;
+          if (kf >= 0) {  // s* = X exactly
+            const int64_t gi = (int64_t)(baseI + i) * ld + baseJ + j0 + q2;
+            const double xd = f32_as_f64(X);
+            if (xd < D[gi]) {
+              D[gi] = xd;
+              if (P) P[gi] = baseK + kf;
+            }
+            pot &= ~bitq;
           }
         }
       }
     }
   }
-  // Pass 2b (path matrix only): the remaining quick improvements, walked as
-  // one stream four at a time; lane l tests k = 4l..4l+3.  Only a k with
-  // lo_k = X can carry the exact sum X, so the lower-bound rows load first
-  // (two float4 per output) and a hit fetches its upper bounds (and, if they
-  // differ, its FP64 operands) alone.  The candidate that attains min up has
-  // lo = up = X, so every quick output has a hit.
-  {
-    unsigned wq = __reduce_or_sync(kFullMask, quick_left), balq = 0u;
-    int posq = 0;
-    auto nextq = [&](int &t, int &sj) -> bool {  // warp-uniform
-      while (!balq) {
-        if (!wq) return false;
-        posq = __ffs(wq) - 1;
-        wq &= wq - 1;
-        balq = __ballot_sync(kFullMask, (quick_left >> posq) & 1u);
-      }
-      const int src = __ffs(balq) - 1;
-      balq &= balq - 1;
-      t = posq >> 1;
-      sj = 2 * src + (posq & 1);
-      return true;
-    };
-#pragma unroll 1
-    for (;;) {
-      int t[4], sj[4];
-      bool v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = nextq(t[u], sj[u]);
-      if (!v[0]) break;
-      float4 al[4], bl[4];
-      float X[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (!v[u]) continue;
-        const int i = i0 + t[u];
-        al[u] = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
-        bl[u] = reinterpret_cast<const float4 *>(&B->rlo[jb0 + sj[u]][0])[lane];
-        X[u] = Lo[i * H + sj[u]];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (!v[u]) continue;
-        const int i = i0 + t[u], jb = jb0 + sj[u];
-        const float la[4] = {al[u].x, al[u].y, al[u].z, al[u].w};
-        const float lb[4] = {bl[u].x, bl[u].y, bl[u].z, bl[u].w};
-        unsigned h = 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int k = 4 * lane + q;
-          if (__fadd_rd(la[q], lb[q]) == X[u] &&
-              (__fadd_ru(A->rhi[i][k], B->rhi[jb][k]) == X[u] ||
-               __dadd_rn(A->r64[i][k], B->r64[jb][k]) == __longlong_as_double((long long)f32_to_f64_bits(X[u]))))
-            h |= 1u << q;
-        }
-        const unsigned hb = __ballot_sync(kFullMask, h != 0u);
-        const int L = __ffs(hb) - 1;
-        const unsigned hL = __shfl_sync(kFullMask, h, L & 31);
-        if (lane == 0 && hb) P[(int64_t)(baseI + i) * ld + baseJ + sj[u]] = baseK + 4 * L + (__ffs(hL) - 1);
-      }
-    }
-  }
-  // Pass 2c: the slow outputs (bounds that do not decide; real weights), the
-  // warp's flagged outputs walked as one stream two at a time (the bound rows
-  // of both load together); lane l tests k = 4l..4l+3: exact FP64 minimum over
-  // the candidates with lo <= min(up, ru(old)), first k on ties.
-  const unsigned todo = slow;
-  unsigned wf = __reduce_or_sync(kFullMask, todo);
-  unsigned bal = 0u;
+  // Pass 2b: every remaining candidate output, walked as one stream two at a
+  // time; lane l tests k = 4l..4l+3.  The lower-bound rows load first; a k
+  // with lo_k = X fetches its upper bounds (and, if they differ, its FP64
+  // operands).  The first exact X settles the output; without one, the exact
+  // FP64 minimum over the candidates with lo_k <= min(ru(old), min up over
+  // lo_k = X) does (first k on ties).
+  unsigned wf = __reduce_or_sync(kFullMask, pot), bal = 0u;
   int pos = 0;
-  auto next = [&](int &t, int &sj, bool &is_slow) -> bool {  // warp-uniform
+  auto next = [&](int &t, int &sj) -> bool {  // warp-uniform
     while (!bal) {
       if (!wf) return false;
       pos = __ffs(wf) - 1;
       wf &= wf - 1;
-      bal = __ballot_sync(kFullMask, (todo >> pos) & 1u);
+      bal = __ballot_sync(kFullMask, (pot >> pos) & 1u);
     }
     const int src = __ffs(bal) - 1;
     bal &= bal - 1;
     t = pos >> 1;
     sj = 2 * src + (pos & 1);
-    is_slow = (__shfl_sync(kFullMask, slow, src) >> pos) & 1u;
     return true;
   };
 #pragma unroll 1
   for (;;) {
     int t[2], sj[2];
-    bool sl[2], v[2];
+    bool v[2];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) v[u] = next(t[u], sj[u], sl[u]);
+    for (int u = 0; u < 2; ++u) v[u] = next(t[u], sj[u]);
     if (!v[0]) break;
-    float4 alo[2], ahi[2], blo[2], bhi[2];
+    float4 al[2], bl[2];
     double old[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (!v[u]) continue;
       const int i = i0 + t[u];
-      alo[u] = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
-      ahi[u] = reinterpret_cast<const float4 *>(&A->rhi[i][0])[lane];
-      blo[u] = reinterpret_cast<const float4 *>(&B->rlo[jb0 + sj[u]][0])[lane];
-      bhi[u] = reinterpret_cast<const float4 *>(&B->rhi[jb0 + sj[u]][0])[lane];
-      old[u] = D[(int64_t)(baseI + i) * ld + baseJ + sj[u]];  // quick: already the new value (unused)
+      al[u] = reinterpret_cast<const float4 *>(&A->rlo[i][0])[lane];
+      bl[u] = reinterpret_cast<const float4 *>(&B->rlo[jb0 + sj[u]][0])[lane];
+      old[u] = D[(int64_t)(baseI + i) * ld + baseJ + sj[u]];
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (!v[u]) continue;
-      const int i = i0 + t[u];
-      const int64_t g = (int64_t)(baseI + i) * ld + baseJ + sj[u];
+      const int i = i0 + t[u], jb = jb0 + sj[u];
+      const int64_t gi = (int64_t)(baseI + i) * ld + baseJ + sj[u];
       const float X = Lo[i * H + sj[u]];
-      const float th = sl[u] ? fminf(Up[i * H + sj[u]], f64_up(old[u])) : X;
-      const float la[4] = {alo[u].x, alo[u].y, alo[u].z, alo[u].w};
-      const float ha[4] = {ahi[u].x, ahi[u].y, ahi[u].z, ahi[u].w};
-      const float lb[4] = {blo[u].x, blo[u].y, blo[u].z, blo[u].w};
-      const float hb[4] = {bhi[u].x, bhi[u].y, bhi[u].z, bhi[u].w};
+      const float la[4] = {al[u].x, al[u].y, al[u].z, al[u].w};
+      const float lb[4] = {bl[u].x, bl[u].y, bl[u].z, bl[u].w};
+      float l4[4];
+      unsigned h = 0u;
+      float upx = FINF;  // min up over this lane's k with lo_k = X
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * lane + q;
+        l4[q] = __fadd_rd(la[q], lb[q]);
+        if (l4[q] == X) {
+          const float up_ = __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
+          upx = fminf(upx, up_);
+          if (up_ == X || __dadd_rn(A->r64[i][k], B->r64[jb][k]) == f32_as_f64(X)) h |= 1u << q;
+        }
+      }
+      const unsigned hb = __ballot_sync(kFullMask, h != 0u);
+      if (hb) {  // s* = X exactly; the lowest hit is the first k
+        const int L = __ffs(hb) - 1;
+        const unsigned hL = __shfl_sync(kFullMask, h, L);
+        const double xd = f32_as_f64(X);
+        if (lane == 0 && xd < old[u]) {
+          D[gi] = xd;
+          if (P) P[gi] = baseK + 4 * L + (__ffs(hL) - 1);
+        }
+        continue;
+      }
+      // s* > X: exact FP64 minimum over the candidates that can reach it.
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) upx = fminf(upx, __shfl_xor_sync(kFullMask, upx, off));
+      const float th = fminf(upx, f64_up(old[u]));
       long long best = 0x7fffffffffffffffll;
       int bestk = 0x7fffffff;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int k = 4 * lane + q;
-        const float l = __fadd_rd(la[q], lb[q]);
-        if (l <= th) {
-          const float up_ = __fadd_ru(ha[q], hb[q]);
-          unsigned long long vb;
-          if (l == up_) vb = f32_to_f64_bits(l);
-          else vb = (unsigned long long)__double_as_longlong(__dadd_rn(A->r64[i][k], B->r64[jb0 + sj[u]][k]));
+        if (l4[q] <= th) {
+          const float up_ = __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
+          const unsigned long long vb =
+              l4[q] == up_ ? f32_to_f64_bits(l4[q])
+                           : (unsigned long long)__double_as_longlong(__dadd_rn(A->r64[i][k], B->r64[jb][k]));
           const long long key = dkey(vb);
           if (key < best) {
             best = key;
@@ -697,15 +642,10 @@ __global__ void __launch_bounds__(THREADS, 2)
           bestk = okk;
         }
       }
-      if (lane == 0 && bestk != 0x7fffffff) {
-        if (sl[u]) {
-          if (best < dkey((unsigned long long)__double_as_longlong(old[u]))) {
-            D[g] = __longlong_as_double((long long)dkey_bits(best));
-            if (P) P[g] = baseK + bestk;
-          }
-        } else if (P) {
-          P[g] = baseK + bestk;
-        }
+      if (lane == 0 && bestk != 0x7fffffff &&
+          best < dkey((unsigned long long)__double_as_longlong(old[u]))) {
+        D[gi] = __longlong_as_double((long long)dkey_bits(best));
+        if (P) P[gi] = baseK + bestk;
       }
     }
   }
