@@ -190,10 +190,11 @@ int apsp_profile_enable(int on);
 /* Measured ceiling of the relaxation on this GPU (a measurement hook; the
  * paper quotes datasheet peaks only, Table 1): runs the inner-loop
  * instruction pair of the FP32 kernels (dtype_bytes = 4: packed add.rn.f32x2
- * + three-input min) or of the FP64 interval path (dtype_bytes = 8) on
- * registers only, on every SM, and writes the relaxations per clock per SM
- * it sustains.  Synchronises `stream`; uses and frees stream-ordered scratch.
- * Returns APSP_EINVAL for other dtype_bytes or a NULL output. */
+ * + three-input min) or of the FP64 path's lower-bound loop (dtype_bytes = 8:
+ * add.rm.f32x2 + three-input min) on registers only, on every SM, and writes
+ * the relaxations per clock per SM it sustains.  Synchronises `stream`; uses
+ * and frees stream-ordered scratch.  Returns APSP_EINVAL for other
+ * dtype_bytes or a NULL output. */
 int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm, void *stream);
 
 /* Synchronizes `stream`, then returns and clears the error word that the

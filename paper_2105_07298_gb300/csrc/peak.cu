@@ -7,8 +7,8 @@
 // with no memory traffic, and times itself with the SM clock.  Every packed
 // add takes its previous result as an operand, so the compiler can neither
 // hoist nor merge adds (loop-invariant operands would let it, and the rate
-// would come out too high).  The FP64 variant runs the interval pair
-// (add.rm + add.rp, two mins) that the FP64 path uses per pair of relaxations.
+// would come out too high).  The FP64 variant runs the pair of the FP64
+// path's main loop: the same with add.rm.f32x2 (lower bounds).
 #include <stdint.h>
 
 #include "common.cuh"
@@ -39,15 +39,11 @@ __global__ void __launch_bounds__(256) peak_kernel(float *out, unsigned long lon
         asm volatile("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
                      : "+f"(acc[j])
                      : "l"(t[j]));
-      } else {  // lower and upper bound of the same two candidates
+      } else {  // lower bounds of two candidates (the FP64 path's main loop)
         asm volatile("add.rm.f32x2 %0, %0, %1;" : "+l"(t[j]) : "l"(c));
         asm volatile("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
                      : "+f"(acc[j])
                      : "l"(t[j]));
-        asm volatile("add.rp.f32x2 %0, %0, %1;" : "+l"(u[j]) : "l"(c));
-        asm volatile("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\tmin.f32 %0, %0, lo, hi;\n\t}"
-                     : "+f"(acc2[j])
-                     : "l"(u[j]));
       }
     }
   }
@@ -105,8 +101,8 @@ APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm,
   unsigned long long mx = 1;
   for (int i = 0; i < blocks; ++i) mx = h[i] > mx ? h[i] : mx;
   delete[] h;
-  // all blocks are resident at once; relaxations per pair-instruction: 2
-  // (FP32) or 2 FP64 relaxations per interval pair.
+  // all blocks are resident at once; two relaxations (FP32, or FP64 lower
+  // bounds) per instruction pair.
   const double relax = 2.0 * 16.0 * iters * (double)threads * blocks;
   *relax_per_clk_per_sm = relax / sms / (double)mx;
   return APSP_OK;
