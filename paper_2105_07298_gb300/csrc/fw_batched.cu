@@ -73,19 +73,23 @@ union BatchedSmem {
   mp32::DiagSmemT<64> diag;
 };
 
-__device__ __forceinline__ void relax2_argmin(float &acc, int &idx, unsigned long long a,
-                                              unsigned long long b, int k0) {
-  float c0, m;
-  asm("{\n\t.reg .b64 t;\n\t.reg .f32 hi;\n\t"
-      "add.rn.f32x2 t, %2, %3;\n\t"
-      "mov.b64 {%0, hi}, t;\n\t"
-      "min.f32 %1, %4, %0, hi;\n\t}"
-      : "=f"(c0), "=f"(m)
+// Eager path tracking per k-pair: the three-input min writes the new
+// accumulator, and the pair index is kept when it lowered the accumulator
+// strictly.  Which k of the last such pair reached the final value is settled
+// once per output after the loop (the lower k if its candidate equals the
+// final value: the strict "<" of the sequential loop keeps the first k
+// reaching a minimum).
+__device__ __forceinline__ void relax2_argpair(float &acc, int &kp_last, unsigned long long a,
+                                               unsigned long long b, int kp) {
+  float m;
+  asm("{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
+      "add.rn.f32x2 t, %1, %2;\n\t"
+      "mov.b64 {lo, hi}, t;\n\t"
+      "min.f32 %0, %3, lo, hi;\n\t}"
+      : "=f"(m)
       : "l"(a), "l"(b), "f"(acc));
-  if (m < acc) {
-    idx = (c0 == m) ? k0 : k0 + 1;  // the lower k wins a tie inside the pair
-    acc = m;
-  }
+  kp_last = m < acc ? kp : kp_last;
+  acc = m;
 }
 
 // C(baseI, baseJ) <- min(C, A(baseI, baseK) (x) B(baseK, baseJ)), TB = 64,
@@ -133,7 +137,7 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
       kid[a][c] = -1;
     }
   const int kpn = (mK + 1) / 2;
-#pragma unroll 2
+#pragma unroll 1
   for (int kp = 0; kp < kpn; ++kp) {
     unsigned long long a[TM], b[TM];
 #pragma unroll
@@ -152,8 +156,20 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
     for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
       for (int cc = 0; cc < TM; ++cc) {
-        if (EAGER) relax2_argmin(acc[rr][cc], kid[rr][cc], a[rr], b[cc], 2 * kp);
+        if (EAGER) relax2_argpair(acc[rr][cc], kid[rr][cc], a[rr], b[cc], kp);
         else mp32::relax2(acc[rr][cc], a[rr], b[cc]);
+      }
+  }
+  if (EAGER) {  // the k inside each output's last improving pair
+#pragma unroll
+    for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < TM; ++cc) {
+        const int kp = kid[rr][cc];
+        if (kp >= 0) {
+          const float2 c = mp32::sum2(sm.As[kp][row_at(rr, ty)], sm.Bs[kp][col_at(cc, tx)]);
+          kid[rr][cc] = c.x == acc[rr][cc] ? 2 * kp : 2 * kp + 1;
+        }
       }
   }
   // Epilogue: candidates (and eager argmins) to shared memory; each warp
