@@ -62,12 +62,15 @@ constexpr int kDenseMin64 = APSP_F64_DENSE_MIN;
 // (transposed).  The paired arrays are split in two 64-wide halves so that a
 // 16-k-pair slab of one half is one contiguous 8 KiB piece.  Entries outside
 // the matrix hold +inf.
-struct Pack {
+// 128-byte aligned so that every pack of an array starts on a 16-byte
+// boundary (bulk copies and 16-byte loads read from it).
+struct __align__(128) Pack {
   unsigned long long lo[2][T / 2][T / 2];
   unsigned long long hi[2][T / 2][T / 2];
   float rlo[T][T];
   float rhi[T][T];
   double r64[T][T];
+  int exact;  // 1: every value is a float (rlo == rhi), so upper bounds follow from rlo
 };
 
 // ---------------------------------------------------------------- bounds
@@ -157,6 +160,7 @@ __device__ __forceinline__ void relax2_rp(float &acc, unsigned long long a, unsi
 // an A operand (as_b = false) or a B operand (as_b = true).
 template <int S>
 __device__ void pack_block(const double *s, Pack *pk, bool as_b) {
+  bool ex = true;
   for (int e = threadIdx.x; e < T * T / 2; e += blockDim.x) {
     const int kp = e / T, x = e % T;
     const double v0 = as_b ? s[(2 * kp) * S + x] : s[x * S + 2 * kp];
@@ -167,10 +171,14 @@ __device__ void pack_block(const double *s, Pack *pk, bool as_b) {
   for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
     const int x = e / T, k = e % T;  // row x of the row-contiguous copies
     const double v = as_b ? s[k * S + x] : s[x * S + k];
-    pk->rlo[x][k] = f64_down(v);
-    pk->rhi[x][k] = f64_up(v);
+    const float vl = f64_down(v), vh = f64_up(v);
+    pk->rlo[x][k] = vl;
+    pk->rhi[x][k] = vh;
     pk->r64[x][k] = v;
+    ex = ex && vl == vh;
   }
+  const int all = __syncthreads_and(ex);
+  if (threadIdx.x == 0) pk->exact = all;
 }
 
 // ---------------------------------------------------------------- K1
@@ -363,6 +371,10 @@ __global__ void __launch_bounds__(THREADS, 3)
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ty = 4 * w + (lane >> 3), tx = lane & 7;
   const float FINF = __int_as_float(0x7f800000);
+  // Both operands hold floats only: a candidate's upper bound is ru of the
+  // same operands as its lower bound (read once here: phases 2/3 may clear
+  // the flag of the pack they re-pack while a sibling CTA still reads it).
+  const bool exact = A->exact && B->exact;
 
   if (tid == 0) {
     for (int st = 0; st < STAGES; ++st) mbar_init(&sm.bar[st], 1);
@@ -511,19 +523,25 @@ __global__ void __launch_bounds__(THREADS, 3)
           const int jb = jb0 + j0 + q2;
           // the chunk's eight lower-bound sums; upper bounds (and FP64 sums)
           // only for a k whose lower bound is X, in ascending k
-          unsigned eq = 0u;
+          unsigned eq = 0u, equp = 0u;  // lo_k = X; and up_k = X (exact operands only)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 l = sum2_rm(__ldg(pal + (4 * c + q) * H), __ldg(pbl + (4 * c + q) * H + q2));
+            const unsigned long long av = __ldg(pal + (4 * c + q) * H), bv = __ldg(pbl + (4 * c + q) * H + q2);
+            const float2 l = sum2_rm(av, bv);
             eq |= (l.x == X ? 1u : 0u) << (2 * q);
             eq |= (l.y == X ? 1u : 0u) << (2 * q + 1);
+            if (exact) {
+              const float2 u = sum2_rp(av, bv);
+              equp |= (u.x == X ? 1u : 0u) << (2 * q);
+              equp |= (u.y == X ? 1u : 0u) << (2 * q + 1);
+            }
           }
           int kf = -1;
 #pragma unroll 1
           while (eq) {
-            const int k = 8 * c + __ffs(eq) - 1;
+            const int b = __ffs(eq) - 1, k = 8 * c + b;
             eq &= eq - 1;
-            if (__fadd_ru(A->rhi[i][k], B->rhi[jb][k]) == X ||
+            if ((exact ? ((equp >> b) & 1u) != 0u : __fadd_ru(A->rhi[i][k], B->rhi[jb][k]) == X) ||
                 __dadd_rn(A->r64[i][k], B->r64[jb][k]) == f32_as_f64(X)) {
               kf = k;
               break;
@@ -596,7 +614,7 @@ __global__ void __launch_bounds__(THREADS, 3)
         const int k = 4 * lane + q;
         l4[q] = __fadd_rd(la[q], lb[q]);
         if (l4[q] == X) {
-          const float up_ = __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
+          const float up_ = exact ? __fadd_ru(la[q], lb[q]) : __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
           upx = fminf(upx, up_);
           if (up_ == X || __dadd_rn(A->r64[i][k], B->r64[jb][k]) == f32_as_f64(X)) h |= 1u << q;
         }
@@ -622,7 +640,7 @@ __global__ void __launch_bounds__(THREADS, 3)
       for (int q = 0; q < 4; ++q) {
         const int k = 4 * lane + q;
         if (l4[q] <= th) {
-          const float up_ = __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
+          const float up_ = exact ? __fadd_ru(la[q], lb[q]) : __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
           const unsigned long long vb =
               l4[q] == up_ ? f32_to_f64_bits(l4[q])
                            : (unsigned long long)__double_as_longlong(__dadd_rn(A->r64[i][k], B->r64[jb][k]));
@@ -653,6 +671,7 @@ __global__ void __launch_bounds__(THREADS, 3)
   // Phases 2/3: re-pack this half of the updated block for the round's phase 4.
   __syncthreads();
   Pack *dst = MODE == 1 ? &packB[J] : &packA[I];
+  bool ex = true;  // every value this CTA re-packs is a float
 #pragma unroll
   for (int rr = 0; rr < 4; rr += 2) {
     const int i0p = row4(rr, ty);  // rows i0p, i0p + 1 of the block
@@ -674,6 +693,7 @@ __global__ void __launch_bounds__(THREADS, 3)
         for (int c = 0; c < 2; ++c) {
           const int i = i0p + a, j = jb + c;
           const float vl = f64_down(v[a][c]), vh = f64_up(v[a][c]);
+          ex = ex && vl == vh;
           if (MODE == 1) {  // B operand: [j][k = i]
             dst->rlo[j][i] = vl;
             dst->rhi[j][i] = vh;
@@ -700,6 +720,9 @@ __global__ void __launch_bounds__(THREADS, 3)
       }
     }
   }
+  // The flag stays 1 only if the values before (packing) and after (both
+  // halves) are all floats; a half with an inexact value clears it.
+  if (__syncthreads_or(!ex) && tid == 0) dst->exact = 0;
 }
 
 static int g_smem_k1[64], g_smem_k2a[64], g_smem_p0[64], g_smem_p1[64], g_smem_p2[64];
