@@ -275,8 +275,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": workload_config(n, world, args.dtype),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
-                             "sample": f"outer k iterations 0..{min(ks)}-1 of classic FW (Algorithm 1) "
-                                       f"on the n={n} graph per step (fixed per-call cost excluded)"},
+                             "sample": f"outer k iterations 0..{min(ks) - 1} (at least) of classic FW "
+                                       f"(Algorithm 1) on the n={n} graph per step (fixed per-call cost excluded)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if world > 1:
