@@ -171,11 +171,147 @@ __global__ void __launch_bounds__(k2::THREADS, 2) fw_phase2_lines_f32(float *__r
 // Grid: (R-1)^2 CTAs in row-major (I', J') order over the blocks I, J != r,
 // so consecutive CTAs share the column-panel block A and sweep the row panel.
 // --------------------------------------------------------------------------
+// K1 (FP32): Algorithm 1 on the diagonal block, minima only in the step
+// loop, path entries recovered afterwards.  Each thread keeps its 8 x 8
+// elements in registers; at step k the owners of row k and column k publish
+// them into a per-step history in shared memory (k-paired layout:
+// hr[k/2][j] = (row 2kp at its step, row 2kp+1 at its step), hc likewise for
+// columns), one barrier per step.  Step k never changes row or column k
+// (D[k][k] = 0), so the published values are the ones every thread uses.
+// Within the round an element's last strict improvement is the first step
+// whose candidate hc[k][i] + hr[k][j] equals the element's final value, so
+// after the loop each improved element finds that k by scanning its
+// candidate sums from the history (folded 8 k at a time, lowest matching
+// chunk kept, then the first k inside it) - the P of the sequential loop.
+namespace k1 {
+constexpr int T = mp32::T, TM = 8;
+struct Hist {
+  unsigned long long hc[T / 2][T];  // (D[i][2kp], D[i][2kp+1]) as published at steps 2kp, 2kp+1
+  unsigned long long hr[T / 2][T];  // (D[2kp][j], D[2kp+1][j]) likewise
+};
+}  // namespace k1
+
 __global__ void __launch_bounds__(mp32::THREADS)
     fw_phase1_diag_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r) {
-  __shared__ mp32::DiagSmem sm;
-  const int base = r * mp32::T;
-  mp32::diag_closure<8>(D, ld, P, base, min(mp32::T, n - base), sm);
+  using namespace k1;
+  using mp32::col_at;
+  using mp32::row_at;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Hist &h = *reinterpret_cast<Hist *>(smem_raw);
+  float *hc = reinterpret_cast<float *>(&h.hc[0][0]), *hr = reinterpret_cast<float *>(&h.hr[0][0]);
+  const int base = r * T, m = min(T, n - base);
+  const int ty = mp32::thread_ty(), tx = mp32::thread_tx();
+  const float INF = inf<float>();
+  float d[TM][TM];
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < TM; ++cc) {
+      const int i = row_at(rr, ty), j = col_at(cc, tx);
+      d[rr][cc] = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : INF;
+    }
+  // k = 32 kb + 2 kk + q: row_at / col_at index 2 kb + q of owner kk; k-pair 16 kb + kk.
+#pragma unroll
+  for (int kb = 0; kb < TM / 2; ++kb) {
+#pragma unroll 1
+    for (int kk = 0; kk < 16; ++kk) {
+      const int kp = 16 * kb + kk;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (ty == kk) {
+#pragma unroll
+          for (int cc = 0; cc < TM; ++cc) hr[(kp * T + col_at(cc, tx)) * 2 + q] = d[2 * kb + q][cc];
+        }
+        if (tx == kk) {
+#pragma unroll
+          for (int rr = 0; rr < TM; ++rr) hc[(kp * T + row_at(rr, ty)) * 2 + q] = d[rr][2 * kb + q];
+        }
+        __syncthreads();
+        float a[TM], b[TM];
+#pragma unroll
+        for (int rr = 0; rr < TM; ++rr) a[rr] = hc[(kp * T + row_at(rr, ty)) * 2 + q];
+#pragma unroll
+        for (int cc = 0; cc < TM; ++cc) b[cc] = hr[(kp * T + col_at(cc, tx)) * 2 + q];
+#pragma unroll
+        for (int rr = 0; rr < TM; ++rr) {
+          const unsigned long long aa = mp32::pack2(a[rr], a[rr]);
+#pragma unroll
+          for (int c2 = 0; c2 < TM / 2; ++c2) {
+            const float2 cand = mp32::sum2(aa, mp32::pack2(b[2 * c2], b[2 * c2 + 1]));
+            d[rr][2 * c2] = fminf(d[rr][2 * c2], cand.x);
+            d[rr][2 * c2 + 1] = fminf(d[rr][2 * c2 + 1], cand.y);
+          }
+        }
+      }
+    }
+  }
+  // D where improved (the old value is still in global memory).
+  unsigned long long imp = 0ull;  // bit 8 rr + cc
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < TM; ++cc) {
+      const int i = row_at(rr, ty), j = col_at(cc, tx);
+      if (i < m && j < m) {
+        const int64_t g = (int64_t)(base + i) * ld + base + j;
+        if (d[rr][cc] < D[g]) {
+          D[g] = d[rr][cc];
+          imp |= 1ull << (TM * rr + cc);
+        }
+      }
+    }
+  if (!P || __syncthreads_count(imp != 0ull) == 0) return;  // the history is complete past this barrier
+  if (imp == 0ull) return;
+  // P: lowest 8-k chunk (4 k-pairs) whose minimum candidate equals the final
+  // value, then the first k inside it.  Chunks are walked from high to low
+  // and the byte of an element is overwritten on every match.
+  unsigned ch[TM][TM / 4];
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int c4 = 0; c4 < TM / 4; ++c4) ch[rr][c4] = 0u;
+#pragma unroll 1
+  for (int c = T / 8 - 1; c >= 0; --c) {
+    unsigned long long bq[4][TM];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int cc = 0; cc < TM; ++cc) bq[q][cc] = h.hr[4 * c + q][col_at(cc, tx)];
+#pragma unroll
+    for (int rr = 0; rr < TM; ++rr) {
+      unsigned long long aq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) aq[q] = h.hc[4 * c + q][row_at(rr, ty)];
+#pragma unroll
+      for (int cc = 0; cc < TM; ++cc) {
+        const float2 s0 = mp32::sum2(aq[0], bq[0][cc]), s1 = mp32::sum2(aq[1], bq[1][cc]);
+        const float2 s2 = mp32::sum2(aq[2], bq[2][cc]), s3 = mp32::sum2(aq[3], bq[3][cc]);
+        float mm = mp32::min3f(s0.x, s0.y, s1.x);
+        mm = mp32::min3f(mm, s1.y, s2.x);
+        mm = mp32::min3f(mm, s2.y, s3.x);
+        mm = fminf(mm, s3.y);
+        if (mm == d[rr][cc])
+          ch[rr][cc / 4] = __byte_perm(ch[rr][cc / 4], (unsigned)c,
+                                       0x3210 ^ ((0x3210 & (0xF << (4 * (cc & 3)))) ^ (4 << (4 * (cc & 3)))));
+      }
+    }
+  }
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < TM; ++cc) {
+      if (!((imp >> (TM * rr + cc)) & 1ull)) continue;
+      const int c = (ch[rr][cc / 4] >> (8 * (cc & 3))) & 0xFF;  // an improved element's chunk
+      const int i = row_at(rr, ty), j = col_at(cc, tx);
+      int kf = 8 * c + 7;
+#pragma unroll
+      for (int q = 3; q >= 0; --q) {
+        const float2 sv = mp32::sum2(h.hc[4 * c + q][i], h.hr[4 * c + q][j]);
+        kf = sv.y == d[rr][cc] ? 8 * c + 2 * q + 1 : kf;
+        kf = sv.x == d[rr][cc] ? 8 * c + 2 * q : kf;
+      }
+      P[(int64_t)(base + i) * ld + base + j] = base + kf;
+    }
 }
 
 // K3 (FP32): one CTA computes one 128 x 64 half of an output block (two CTAs
@@ -525,7 +661,7 @@ std::vector<cudaEvent_t> g_prof_pool;
 constexpr int kMaxN = 65536;
 
 constexpr int kT32 = mp32::T, kT64 = 128;
-static int g_smem_p2f[64], g_smem_k3[64];
+static int g_smem_k1f[64], g_smem_p2f[64], g_smem_k3[64];
 
 int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s);
 int take_device_error_f64();
@@ -550,6 +686,7 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
   const int n = (int)n64;
   constexpr int T = kT32;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if ((st = ensure_smem(fw_phase1_diag_f32, (int)sizeof(k1::Hist), g_smem_k1f))) return st;
   if ((st = ensure_smem(fw_phase2_lines_f32, k2::SMEM, g_smem_p2f))) return st;
   if ((st = ensure_smem(fw_phase3_minplus_f32, (int)sizeof(k3::Smem), g_smem_k3))) return st;
   cudaGetLastError();  // clear any stale error so the checks below are ours
@@ -579,7 +716,7 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
   auto diag_and_panels = [&](int r, cudaStream_t st) {
     {
       PhaseScope ps(1, st);
-      fw_phase1_diag_f32<<<1, mp32::THREADS, 0, st>>>(D, ld, P, n, r);
+      fw_phase1_diag_f32<<<1, mp32::THREADS, sizeof(k1::Hist), st>>>(D, ld, P, n, r);
     }
     if (R > 1) {
       PhaseScope ps(2, st);
