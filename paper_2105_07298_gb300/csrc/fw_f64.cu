@@ -95,6 +95,21 @@ __device__ __forceinline__ float f64_up(double x) {
 
 __device__ __forceinline__ float f64_down(double x) { return -f64_up(-x); }
 
+// Exact x < d for a float x and a double d (no NaN).  Equal to x < ru(d),
+// since a float below d is below the smallest float >= d.  Both non-negative
+// with x normal: the doubles' bit patterns order as unsigned integers, so x's
+// double pattern is built (exponent rebiased, mantissa shifted) and compared.
+__device__ __forceinline__ bool f32_lt_f64(float x, double d) {
+  const unsigned ux = __float_as_uint(x);
+  const unsigned long long ud = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = ux >> 23;  // sign bit clear: the biased exponent
+  if (!(ud >> 63) && e - 1u < 254u) {
+    const unsigned long long bx = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(ux & 0x7fffffu) << 29);
+    return bx < ud;
+  }
+  return x < f64_up(d);
+}
+
 // Exact float -> double bits (integer pipes; subnormal floats via cvt).
 __device__ __forceinline__ unsigned long long f32_to_f64_bits(float f) {
   const unsigned u = __float_as_uint(f);
@@ -456,8 +471,8 @@ __global__ void __launch_bounds__(THREADS, 3)
     for (int t = 0; t < 8; ++t) {
       const float2 x = *reinterpret_cast<const float2 *>(&Lo[(i0 + t8 + t) * H + j0]);
       if (i0 + t8 + t < mI) {
-        if (j0 < mJ && x.x < f64_up(o[t][0])) pot |= 1u << (2 * (t8 + t));
-        if (j0 + 1 < mJ && x.y < f64_up(o[t][1])) pot |= 2u << (2 * (t8 + t));
+        if (j0 < mJ && f32_lt_f64(x.x, o[t][0])) pot |= 1u << (2 * (t8 + t));
+        if (j0 + 1 < mJ && f32_lt_f64(x.y, o[t][1])) pot |= 2u << (2 * (t8 + t));
       }
     }
   }
