@@ -74,9 +74,16 @@ int apsp_fw_block_size(int elem_bytes);
  *   ld     : leading dimension in elements, ld >= max(n, 1).
  *   d_path : optional n x n int32 path matrix with the same ld; when non-NULL
  *            it is fully written (P as described above).  May be NULL.
- *   stream : cudaStream_t as void*.
- * Returns APSP_OK, APSP_EINVAL (null d_dist with n > 0, ld < n, n > 65536)
- * or APSP_ECUDA.
+ *   stream : cudaStream_t as void*.  All work is ordered after earlier work
+ *            on `stream`, and later work on `stream` sees the results.  With
+ *            more than two blocks per side the next round's phases 1-3 run
+ *            on an internal second stream (created and destroyed by the call,
+ *            joined to `stream` by events), except while `stream` is being
+ *            captured into a CUDA graph: then every phase runs on `stream`.
+ *            Scratch (operand panels, about 32 n (TB + 1) bytes) is
+ *            stream-ordered (cudaMallocAsync / cudaFreeAsync on `stream`).
+ * Returns APSP_OK, APSP_EINVAL (null d_dist with n > 0, ld < n, n > 65536),
+ * APSP_ENOMEM (scratch) or APSP_ECUDA.
  * ---------------------------------------------------------------------- */
 int apsp_fw_f32(float *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
 int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);

@@ -797,7 +797,15 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
   // pack set).
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_next = nullptr, ev_panels = nullptr;
-  if (R > 2) {
+  // While the caller's stream is being captured into a CUDA graph every
+  // phase stays on that stream (no stream is created or destroyed mid-capture).
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    if (scratch) cudaFreeAsync(scratch, s);
+    cudaGetLastError();
+    return APSP_ECUDA;
+  }
+  if (R > 2 && cap == cudaStreamCaptureStatusNone) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, hi) != cudaSuccess ||

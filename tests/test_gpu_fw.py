@@ -253,3 +253,29 @@ def test_measured_pair_rate_is_plausible():
     assert 0.85 * r32 < r64 < 1.15 * r32, (r32, r64)
     with pytest.raises(apsp.ApspError):
         apsp.measure_peak(2)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_solve_captured_in_cuda_graph(dtype):
+    """A solve captured into a CUDA graph (all phases on the capturing stream)
+    replays to the same D and P as a direct call."""
+    n = 700
+    W = torch.from_numpy(graphgen.dense_graph(n, 0.4, 77, dtype=dtype)).to(DEV)
+    D0, P0 = W.clone(), torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.apsp_fw(D0, P0)
+    D, P = W.clone(), torch.empty((n, n), dtype=torch.int32, device=DEV)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        apsp.apsp_fw(D, P)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        D.copy_(W)
+        apsp.apsp_fw(D, P)
+    P.fill_(-7)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(D, D0) and torch.equal(P, P0)
+    assert apsp.device_status() == apsp.APSP_OK
