@@ -80,8 +80,9 @@ int apsp_fw_block_size(int elem_bytes);
  *            on an internal second stream (created and destroyed by the call,
  *            joined to `stream` by events), except while `stream` is being
  *            captured into a CUDA graph: then every phase runs on `stream`.
- *            Scratch (operand panels, about 32 n (TB + 1) bytes) is
- *            stream-ordered (cudaMallocAsync / cudaFreeAsync on `stream`).
+ *            Scratch (operand panels: about 32 n TB bytes for FP32, 96 n TB
+ *            bytes for FP64; 128 MiB / 384 MiB at n = 32768) is stream-ordered
+ *            (cudaMallocAsync / cudaFreeAsync on `stream`).
  * Returns APSP_OK, APSP_EINVAL (null d_dist with n > 0, ld < n, n > 65536),
  * APSP_ENOMEM (scratch) or APSP_ECUDA.
  * ---------------------------------------------------------------------- */
