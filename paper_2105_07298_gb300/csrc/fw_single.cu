@@ -344,7 +344,16 @@ struct Smem {
 #ifndef APSP_K3_MIN_BLOCKS
 #define APSP_K3_MIN_BLOCKS 3
 #endif
-__global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
+#ifndef APSP_K3_EAGER_ROUNDS
+#define APSP_K3_EAGER_ROUNDS 16
+#endif
+// Rounds that track P in the main loop (EAGER): in the first rounds nearly
+// every output improves, and one compare and one byte permute per k-pair
+// cost less than recomputing every candidate afterwards.
+constexpr int kEagerRounds = APSP_K3_EAGER_ROUNDS;
+
+template <bool EAGER>
+__global__ void __launch_bounds__(mp32::THREADS, EAGER ? 2 : APSP_K3_MIN_BLOCKS)
     fw_phase3_minplus_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
                           int R, int vec_ok, Panels pan, int set) {
   using namespace k3;
@@ -399,10 +408,13 @@ __global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
   __syncthreads();
 
   float acc[8][4];
+  unsigned kid[8];  // EAGER: byte c of kid[a] = the round's k-pair of the last strict decrease, 0xFF none
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 8; ++a) {
+    kid[a] = 0xFFFFFFFFu;
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[a][c] = INF;
+  }
 
   for (int s = 0; s < nslab; ++s) {
     const int st = s % STAGES;
@@ -430,6 +442,7 @@ __global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
         b[cc + 1] = t.y;
       }
     };
+    const unsigned kbase = (unsigned)(s * KP);
     auto compute = [&](int kp, const unsigned long long (&b)[4]) {
       ulonglong2 an = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(0, ty)]);
 #pragma unroll
@@ -438,8 +451,19 @@ __global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
         if (rp < 3) an = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(2 * rp + 2, ty)]);
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          mp32::relax2(acc[2 * rp][cc], ac.x, b[cc]);
-          mp32::relax2(acc[2 * rp + 1][cc], ac.y, b[cc]);
+          if constexpr (EAGER) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float m = mp32::min3f_pair(acc[2 * rp + h][cc], h ? ac.y : ac.x, b[cc]);
+              if (m < acc[2 * rp + h][cc])
+                kid[2 * rp + h] = __byte_perm(kid[2 * rp + h], kbase + kp,
+                                              0x3210 ^ ((0x3210 & (0xF << (4 * cc))) ^ (4 << (4 * cc))));
+              acc[2 * rp + h][cc] = m;
+            }
+          } else {
+            mp32::relax2(acc[2 * rp][cc], ac.x, b[cc]);
+            mp32::relax2(acc[2 * rp + 1][cc], ac.y, b[cc]);
+          }
         }
       }
     };
@@ -467,13 +491,18 @@ __global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
   // owning 16 whole rows (lane l: columns 2l, 2l+1), which keeps the code small
   // (instruction-cache friendly) and every global access coalesced.
   float *Cs = reinterpret_cast<float *>(smem_raw);  // [T][H]
+  unsigned char *Ks = smem_raw + sizeof(Smem::As);  // EAGER: [T][H] k-pair bytes, in the B ring
   __syncthreads();
 #pragma unroll
   for (int rr = 0; rr < 8; ++rr)
 #pragma unroll
-    for (int cc = 0; cc < 4; cc += 2)
+    for (int cc = 0; cc < 4; cc += 2) {
       *reinterpret_cast<float2 *>(&Cs[row_at(rr, ty) * H + col_at(cc, tx)]) =
           make_float2(acc[rr][cc], acc[rr][cc + 1]);
+      if constexpr (EAGER)
+        *reinterpret_cast<unsigned short *>(&Ks[row_at(rr, ty) * H + col_at(cc, tx)]) =
+            (unsigned short)(kid[rr] >> (8 * cc));
+    }
   __syncthreads();
   const float *acp = pan.Acp + (int64_t)I * T * T;
   const float *bt = pan.Bt + ((int64_t)J * T + hJ * H) * T;
@@ -514,6 +543,22 @@ __global__ void __launch_bounds__(mp32::THREADS, APSP_K3_MIN_BLOCKS)
     }
   }
   if (!P) return;
+  if constexpr (EAGER) {
+    // The k inside each improved output's last decreasing pair: the lower one
+    // if its candidate equals the new value (the sequential loop keeps the
+    // first k reaching a minimum).
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!((flags >> (2 * t + q)) & 1u)) continue;
+        const int i = i0 + t, j = j0 + q;
+        const int kp = Ks[i * H + j];  // an improved output has one
+        const float2 c = mp32::sum2(srcA[(int64_t)kp * T + i], srcB[(int64_t)kp * H + j]);
+        P[(int64_t)(baseI + i) * ld + baseJ + j] = baseK + (c.x == Cs[i * H + j] ? 2 * kp : 2 * kp + 1);
+      }
+    return;
+  }
   // Pass 2a: each 8-row group of the warp with many improved outputs (the
   // early rounds, where most outputs improve) is resolved lane-parallel: lane
   // l scans the 128 candidates of its own two columns in the paired panel
@@ -661,7 +706,7 @@ std::vector<cudaEvent_t> g_prof_pool;
 constexpr int kMaxN = 65536;
 
 constexpr int kT32 = mp32::T, kT64 = 128;
-static int g_smem_k1f[64], g_smem_p2f[64], g_smem_k3[64];
+static int g_smem_k1f[64], g_smem_p2f[64], g_smem_k3[64], g_smem_k3e[64];
 
 int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s);
 int take_device_error_f64();
@@ -688,7 +733,8 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if ((st = ensure_smem(fw_phase1_diag_f32, (int)sizeof(k1::Hist), g_smem_k1f))) return st;
   if ((st = ensure_smem(fw_phase2_lines_f32, k2::SMEM, g_smem_p2f))) return st;
-  if ((st = ensure_smem(fw_phase3_minplus_f32, (int)sizeof(k3::Smem), g_smem_k3))) return st;
+  if ((st = ensure_smem(fw_phase3_minplus_f32<false>, (int)sizeof(k3::Smem), g_smem_k3))) return st;
+  if ((st = ensure_smem(fw_phase3_minplus_f32<true>, (int)sizeof(k3::Smem), g_smem_k3e))) return st;
   cudaGetLastError();  // clear any stale error so the checks below are ours
   const int R = (n + T - 1) / T;
   // Phase-4 operand panels, written by K2 each round: two sets (round parity)
@@ -726,8 +772,12 @@ static int run_fw_f32(float *D, int64_t n64, int64_t ld, int32_t *P, void *strea
   auto phase4 = [&](int r, int set, int blocks) {
     if (blocks <= 0) return;
     PhaseScope ps(3, s);
-    fw_phase3_minplus_f32<<<2 * blocks, mp32::THREADS, sizeof(k3::Smem), s>>>(D, ld, P, n, r, R, vec_ok,
-                                                                             pan[r & 1], set);
+    if (P && r < kEagerRounds)
+      fw_phase3_minplus_f32<true><<<2 * blocks, mp32::THREADS, sizeof(k3::Smem), s>>>(D, ld, P, n, r, R, vec_ok,
+                                                                                   pan[r & 1], set);
+    else
+      fw_phase3_minplus_f32<false><<<2 * blocks, mp32::THREADS, sizeof(k3::Smem), s>>>(D, ld, P, n, r, R, vec_ok,
+                                                                                    pan[r & 1], set);
   };
   // Look-ahead: phase 4 of round r first updates row and column r+1 (the
   // blocks K1/K2 of round r+1 read), then the rest of the matrix while K1/K2

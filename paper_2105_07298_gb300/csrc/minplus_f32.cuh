@@ -48,6 +48,18 @@ __device__ __forceinline__ void relax2(float &acc, unsigned long long a, unsigne
       : "l"(a), "l"(b));
 }
 
+// relax2's new accumulator, returned instead of stored (for eager tracking).
+__device__ __forceinline__ float min3f_pair(float acc, unsigned long long a, unsigned long long b) {
+  float m;
+  asm("{\n\t.reg .b64 t;\n\t.reg .f32 lo, hi;\n\t"
+      "add.rn.f32x2 t, %1, %2;\n\t"
+      "mov.b64 {lo, hi}, t;\n\t"
+      "min.f32 %0, %3, lo, hi;\n\t}"
+      : "=f"(m)
+      : "l"(a), "l"(b), "f"(acc));
+  return m;
+}
+
 // The two candidate sums of relax2, unfolded (same rounding).
 __device__ __forceinline__ float2 sum2(unsigned long long a, unsigned long long b) {
   unsigned long long t;
