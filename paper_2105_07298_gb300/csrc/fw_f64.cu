@@ -338,8 +338,17 @@ constexpr int kSetRest = 2;  // the (R-2)^2 blocks off rows/columns r and r+1
 
 __device__ __forceinline__ double f32_as_f64(float x) { return __longlong_as_double((long long)f32_to_f64_bits(x)); }
 
-template <int MODE>
-__global__ void __launch_bounds__(THREADS, 3)
+#ifndef APSP_F64_EAGER_ROUNDS
+#define APSP_F64_EAGER_ROUNDS 16
+#endif
+// Phase-4 rounds whose main loop also keeps, per output, the k-pair where
+// min lo last decreased strictly (EAGER): in the first rounds nearly every
+// output may improve, and one compare and one byte permute per k-pair cost
+// less than scanning every candidate again to find the k that reaches X.
+constexpr int kEagerRounds64 = APSP_F64_EAGER_ROUNDS;
+
+template <int MODE, bool EAGER = false>
+__global__ void __launch_bounds__(THREADS, EAGER ? 2 : 3)
     fw64_product(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R,
                  Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB, int set) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -399,10 +408,13 @@ __global__ void __launch_bounds__(THREADS, 3)
   __syncthreads();
 
   float lo[4][8];
+  unsigned kid[4][2];  // EAGER: byte c%4 of kid[a][c/4] = k-pair of the last strict decrease, 0xFF none
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 4; ++a) {
+    kid[a][0] = kid[a][1] = 0xFFFFFFFFu;
 #pragma unroll
     for (int c = 0; c < 8; ++c) lo[a][c] = FINF;
+  }
 
   for (int s = 0; s < nslab; ++s) {
     const int st = s % STAGES;
@@ -435,7 +447,18 @@ __global__ void __launch_bounds__(THREADS, 3)
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) relax2_rm(lo[rr][cc], a[rr], b[cc]);
+        for (int cc = 0; cc < 8; ++cc) {
+          if constexpr (EAGER) {
+            const float2 t2 = sum2_rm(a[rr], b[cc]);
+            const float m = min3f(lo[rr][cc], t2.x, t2.y);
+            if (m < lo[rr][cc])
+              kid[rr][cc >> 2] = __byte_perm(kid[rr][cc >> 2], (unsigned)(s * KP + kp),
+                                             0x3210 ^ ((0x3210 & (0xF << (4 * (cc & 3)))) ^ (4 << (4 * (cc & 3)))));
+            lo[rr][cc] = m;
+          } else {
+            relax2_rm(lo[rr][cc], a[rr], b[cc]);
+          }
+        }
     }
     __syncthreads();
     if (tid == 0 && s + STAGES < nslab) {
@@ -446,13 +469,18 @@ __global__ void __launch_bounds__(THREADS, 3)
 
   // Epilogue.  The ring is free: X = min lo goes to shared memory, then each
   // warp owns 16 whole rows (lane l: columns 2l, 2l+1 of the half).
-  float *Lo = reinterpret_cast<float *>(smem_raw);  // [T][H]
+  float *Lo = reinterpret_cast<float *>(smem_raw);            // [T][H]
+  unsigned char *Ks = smem_raw + sizeof(ProdSmem::Alo);        // EAGER: [T][H] k-pair bytes
   __syncthreads();
 #pragma unroll
   for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-    for (int cc = 0; cc < 8; cc += 2)
+    for (int cc = 0; cc < 8; cc += 2) {
       *reinterpret_cast<float2 *>(&Lo[row4(rr, ty) * H + col8(cc, tx)]) = make_float2(lo[rr][cc], lo[rr][cc + 1]);
+      if constexpr (EAGER)
+        *reinterpret_cast<unsigned short *>(&Ks[row4(rr, ty) * H + col8(cc, tx)]) =
+            (unsigned short)(kid[rr][cc >> 2] >> (8 * (cc & 3)));
+    }
   __syncthreads();
   const int j0 = 2 * lane, i0 = w * 16, jb0 = hJ * H;
   // Pass 1: outputs that may improve (X < ru(old)).  Bit 2t + q of `pot`:
@@ -476,6 +504,32 @@ __global__ void __launch_bounds__(THREADS, 3)
       }
     }
   }
+  if constexpr (EAGER) {
+    // The k-pair where min lo last decreased holds the first k with lo_k = X
+    // (the lower one if its lower bound is X).  If that candidate's exact sum
+    // is X, s* = X and k is the path entry; otherwise pass 2b decides.
+#pragma unroll 1
+    for (int t = 0; t < 16; ++t)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const unsigned bitq = 1u << (2 * t + q);
+        if (!(pot & bitq)) continue;
+        const int i = i0 + t, jl = j0 + q, jb = jb0 + jl;
+        const int kp = Ks[i * H + jl];  // a candidate output has one (X is finite)
+        const float X = Lo[i * H + jl];
+        const unsigned long long al = A->lo[i >> 6][kp][i & 63], bl = B->lo[hJ][kp][jl];
+        const float2 l = sum2_rm(al, bl);
+        const int k = l.x == X ? 2 * kp : 2 * kp + 1;
+        const float up_ = exact ? (l.x == X ? sum2_rp(al, bl).x : sum2_rp(al, bl).y)
+                                : __fadd_ru(A->rhi[i][k], B->rhi[jb][k]);
+        if (up_ == X || __dadd_rn(A->r64[i][k], B->r64[jb][k]) == f32_as_f64(X)) {
+          const int64_t gi = (int64_t)(baseI + i) * ld + baseJ + jl;
+          D[gi] = f32_as_f64(X);  // X < old (pass 1)
+          if (P) P[gi] = baseK + k;
+          pot &= ~bitq;
+        }
+      }
+  }
   // Pass 2a: each 8-row group of the warp with many candidates (the early
   // rounds) is scanned lane-parallel: lane l walks the lower-bound pairs of
   // its two columns over all k (B pairs coalesced, A pairs broadcast,
@@ -488,7 +542,7 @@ __global__ void __launch_bounds__(THREADS, 3)
 #pragma unroll 1
     for (int G = 0; G < 2; ++G) {
       const unsigned gm = 0xFFFFu << (16 * G);
-      if ((int)__reduce_add_sync(kFullMask, (unsigned)__popc(pot & gm)) < kDenseMin64) continue;
+      if (EAGER || (int)__reduce_add_sync(kFullMask, (unsigned)__popc(pot & gm)) < kDenseMin64) continue;
       const int tg0 = 8 * G;
       float g[8][2];
       unsigned hit[8];  // bit c (+16 for column j0 + 1): chunk c's minimum lo equals X
@@ -740,7 +794,7 @@ __global__ void __launch_bounds__(THREADS, 3)
   if (__syncthreads_or(!ex) && tid == 0) dst->exact = 0;
 }
 
-static int g_smem_k1[64], g_smem_k2a[64], g_smem_p0[64], g_smem_p1[64], g_smem_p2[64];
+static int g_smem_k1[64], g_smem_k2a[64], g_smem_p0[64], g_smem_p0e[64], g_smem_p1[64], g_smem_p2[64];
 
 }  // namespace f64
 
@@ -753,6 +807,7 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
   if ((st = ensure_smem(fw64_diag, smem1, g_smem_k1))) return st;
   if ((st = ensure_smem(fw64_pack_panels, smem2a, g_smem_k2a))) return st;
   if ((st = ensure_smem(fw64_product<0>, smemp, g_smem_p0))) return st;
+  if ((st = ensure_smem(fw64_product<0, true>, smemp, g_smem_p0e))) return st;
   if ((st = ensure_smem(fw64_product<1>, smemp, g_smem_p1))) return st;
   if ((st = ensure_smem(fw64_product<2>, smemp, g_smem_p2))) return st;
   // Operand packs: two sets by round parity (so that phases 1-3 of round
@@ -789,7 +844,10 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
     if (blocks <= 0) return;
     const PackSet &p = ps[r & 1];
     PhaseScope sc(3, s);
-    fw64_product<0><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, set);
+    if (r < kEagerRounds64)
+      fw64_product<0, true><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, set);
+    else
+      fw64_product<0><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, set);
   };
   // Look-ahead as in the FP32 path: phase 4 of round r updates row and
   // column r+1 first; phases 1-3 of round r+1 then run on a second stream of
