@@ -352,8 +352,11 @@ struct Smem {
 // cost less than recomputing every candidate afterwards.
 constexpr int kEagerRounds = APSP_K3_EAGER_ROUNDS;
 
+#ifndef APSP_K3_EAGER_MIN_BLOCKS
+#define APSP_K3_EAGER_MIN_BLOCKS 2
+#endif
 template <bool EAGER>
-__global__ void __launch_bounds__(mp32::THREADS, EAGER ? 2 : APSP_K3_MIN_BLOCKS)
+__global__ void __launch_bounds__(mp32::THREADS, EAGER ? APSP_K3_EAGER_MIN_BLOCKS : APSP_K3_MIN_BLOCKS)
     fw_phase3_minplus_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
                           int R, int vec_ok, Panels pan, int set) {
   using namespace k3;
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(mp32::THREADS, EAGER ? 2 : APSP_K3_MIN_BLOCKS)
     // The k inside each improved output's last decreasing pair: the lower one
     // if its candidate equals the new value (the sequential loop keeps the
     // first k reaching a minimum).
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t < 16; ++t)
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
