@@ -11,17 +11,24 @@
 //                           round's TB values of k.
 // Relaxation rule: Algorithm 1 with a strict "<" (see apsp_fw.h).
 //
+// Rounds overlap: phase 4 of round r first updates row and column r+1, then
+// the rest of the matrix while K1/K2 of round r+1 run on a second stream.
+//
 // Differences from the Pascal design of §3.2 (one output per thread, TB <= 32):
-//  * K3 computes an 8 x 8 register tile per thread (FP32, TB = 128) and pairs
-//    consecutive k: one packed add.rn.f32x2 forms the two candidates of an
-//    output and one three-input min.f32 folds both into the accumulator, so a
-//    relaxation costs one issue slot (FADD2 and FMNMX3 run on different pipes).
-//  * K3 keeps no path state in its inner loop.  After the loop, outputs that
-//    improved (new < old) recover the first k that attains the new minimum:
-//    the 32 lanes of a warp test 32 values of k at a time and take the lowest
-//    hit.  This gives exactly the P of the sequential loop (ascending k,
-//    strict "<" keeps the first k reaching the final minimum) at a cost paid
-//    only by improved outputs.
+//  * K3 runs two CTAs per 128 x 128 block, three per SM, an 8 x 4 register
+//    tile per thread (FP32, TB = 128), and pairs consecutive k: one packed
+//    add.rn.f32x2 forms the two candidates of an output and one three-input
+//    min.f32 folds both into the accumulator (FADD2 and FMNMX3 run on
+//    different pipes).  Operands arrive by bulk copy into a two-stage ring.
+//  * Path state: in rounds 0-15 (nearly every output improves) an eager
+//    instance of K3 keeps, per output, the k-pair of the last strict decrease
+//    as a byte; later rounds keep none in the inner loop, and after the loop
+//    the improved outputs recover the first k that attains the new minimum
+//    (lane-parallel for dense 8-row groups, warp-cooperative otherwise).
+//    Either way P is exactly that of the sequential loop (ascending k, strict
+//    "<" keeps the first k reaching the final minimum).
+//  * K1 keeps only minima in its step loop and recovers P afterwards from a
+//    per-step history; K2 keeps each row/column line in registers.
 //  * Nothing reads P: K1/K2/K3 write P only where D strictly improved.
 #include <stdint.h>
 
