@@ -322,13 +322,16 @@ __global__ void __launch_bounds__(mp32::THREADS)
 }
 
 // K3 (FP32): one CTA computes one 128 x 64 half of an output block (two CTAs
-// per block, three CTAs per SM); each thread owns an 8 x 4 register tile.  The
-// operands come from the panel buffers K2 wrote (already in the paired
-// shared-memory layout and padded with +inf, so the main loop needs no bounds
-// checks): per 32-k slab one 16 KiB bulk copy of A and one 8 KiB copy of B
-// into a two-stage ring, completion tracked by an mbarrier per stage.  Path
-// recovery reads the row-contiguous copies Acp/Bt (one float4 of each per
-// lane: the 128 candidate sums of an output in one memory round trip).
+// per block; three CTAs per SM, two for the eager instance); each thread owns
+// an 8 x 4 register tile.  The operands come from the panel buffers K2 wrote
+// (already in the paired shared-memory layout and padded with +inf, so the
+// main loop needs no bounds checks): per 32-k slab one 16 KiB bulk copy of A
+// and one 8 KiB copy of B into a two-stage ring, completion tracked by an
+// mbarrier per stage.  Path recovery (lazy instance) reads the paired panels
+// lane-parallel for dense row groups, and the row-contiguous copies Acp/Bt
+// otherwise (one float4 of each per lane: the 128 candidate sums of an output
+// in one memory round trip); the eager instance reads one operand pair per
+// improved output.
 namespace k3 {
 constexpr int T = mp32::T, KS = mp32::KS, KP = mp32::KP, STAGES = 2, H = T / 2;
 // Block sets of one phase-4 launch (grid: 2 CTAs per block).
