@@ -29,7 +29,11 @@
 //                        (I,r) <- min(C, C (x) D*(r,r)) (the sequential k loop
 //                        over a panel block equals one product with the
 //                        closure); re-packs the updated blocks.
-//  K3  fw64_product<0>   phase 4: (I,J) <- min(C, D(I,r) (x) D(r,J)).
+//  K3  fw64_product<0>   phase 4: (I,J) <- min(C, D(I,r) (x) D(r,J)); rounds
+//                        0-15 run an eager instance that also keeps, per
+//                        output, the k-pair where min lo last decreased.
+// As in the FP32 path, phase 4 of round r updates row and column r+1 first,
+// then the rest while K1/K2 of round r+1 run on a second stream.
 // On integer-valued weights all sums are exact and D equals every correct FW;
 // on real weights phases 2/3 round through the closure instead of a chain of
 // sums, within the same error bound (relative ~ path length x 2^-53).
