@@ -1,0 +1,63 @@
+"""Host-side logic of bench.py on CPU: the clock/throttle summary, the gate
+that keeps a recorded DRAM traffic figure only for the kernel source it was
+measured on, and the per-round work count of phase 4."""
+import os
+
+import pytest
+
+import bench
+
+
+def _clock_line(sm, smax, power, reasons=("Not Active",) * 5):
+    return ", ".join(["0", str(sm), str(smax), str(power), *reasons]) + "\n"
+
+
+def test_clock_summary_median_power_and_reasons(tmp_path):
+    p = tmp_path / "clk.csv"
+    idle = _clock_line(345, 2070, 90.0)
+    busy = [_clock_line(2070, 2070, 500.0 + i) for i in range(5)]
+    capped = _clock_line(1980, 2070, 640.0, ("Active", "Not Active", "Not Active", "Not Active", "Active"))
+    p.write_text(idle + "".join(busy) + capped + "garbage line\n")
+    c = bench.ClockSampler()
+    c.proc, c.path = object(), str(p)  # as if the sampler had run
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0           # median over loaded samples (power > 200 W)
+    assert s["sm_max_mhz"] == 2070.0
+    assert s["power_w_max"] == 640.0
+    assert s["samples"] == 7
+    assert s["reasons"] == ["sw_power_cap"]
+    assert 500.0 < s["power_w_mean"] < 640.0
+
+
+def test_clock_summary_flags_thermal_slowdown(tmp_path):
+    p = tmp_path / "clk.csv"
+    p.write_text(_clock_line(1500, 2070, 600.0, ("Active", "Not Active", "Active", "Not Active", "Not Active")))
+    c = bench.ClockSampler()
+    c.proc, c.path = object(), str(p)
+    assert c.summary()["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_traffic_kept_only_for_the_measured_source(tmp_path, monkeypatch):
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "phase3_minplus_f32_traffic.txt").write_text(
+        "# comment\nkernel_source_hash: 0123abcd\ndram_bytes_per_round_n32768: 5.5e9\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0123abcd")
+    assert bench.profiled_traffic(32768) == pytest.approx(5.5e9)
+    assert bench.profiled_traffic(16384) is None        # no figure for that size
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "ffffffff")
+    assert bench.profiled_traffic(32768) is None        # kernel changed since the capture
+
+
+def test_committed_traffic_record_is_well_formed():
+    """The committed record names a hash and a per-round byte count."""
+    path = os.path.join(bench.ROOT, "profiles", "phase3_minplus_f32_traffic.txt")
+    txt = open(path).read()
+    assert "kernel_source_hash:" in txt and "dram_bytes_per_round_n32768:" in txt
+
+
+def test_phase4_work_per_round_counts_every_k_of_the_round():
+    # n a multiple of T: every round relaxes (n - T)^2 outputs with T values of k
+    assert bench.phase3_relax_per_round(1024, 128) == pytest.approx((1024 - 128) ** 2 * 128)
+    # a single block has no phase 4
+    assert bench.phase3_relax_per_round(100, 128) == 0
