@@ -140,7 +140,7 @@ __device__ __forceinline__ unsigned long long packf2(float lo, float hi) {
   return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
 }
 
-// The two bound sums of relax2_rm / relax2_rp, unfolded (same rounding).
+// Lower- and upper-bound sums of two candidates (add.rm / add.rp, as the main loop).
 __device__ __forceinline__ float2 sum2_rm(unsigned long long a, unsigned long long b) {
   unsigned long long t;
   asm("add.rm.f32x2 %0, %1, %2;" : "=l"(t) : "l"(a), "l"(b));
@@ -160,14 +160,6 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 __device__ __forceinline__ void relax2_rm(float &acc, unsigned long long a, unsigned long long b) {
   asm("{\n\t.reg .b64 t;\n\t.reg .f32 x, y;\n\t"
       "add.rm.f32x2 t, %1, %2;\n\t"
-      "mov.b64 {x, y}, t;\n\t"
-      "min.f32 %0, %0, x, y;\n\t}"
-      : "+f"(acc)
-      : "l"(a), "l"(b));
-}
-__device__ __forceinline__ void relax2_rp(float &acc, unsigned long long a, unsigned long long b) {
-  asm("{\n\t.reg .b64 t;\n\t.reg .f32 x, y;\n\t"
-      "add.rp.f32x2 t, %1, %2;\n\t"
       "mov.b64 {x, y}, t;\n\t"
       "min.f32 %0, %0, x, y;\n\t}"
       : "+f"(acc)
