@@ -148,7 +148,9 @@ int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, const int32_t *h
 /* Autotuner hook for the batched kernel: per size class (0..3, vertex-count
  * bounds given by apsp_batched_class_bounds) pick the variant index used by
  * later plans.  apsp_batched_num_variants reports how many variants a class
- * has.  Defaults are the built-in table. */
+ * has (variant 0: path entries recovered lazily after each block product;
+ * variant 1: tracked in the inner loop per k-pair; results are identical).
+ * Defaults are the built-in table. */
 int apsp_batched_num_classes(void);
 int apsp_batched_class_bounds(int cls, int32_t *lo, int32_t *hi);
 int apsp_batched_num_variants(int cls);

@@ -1,11 +1,13 @@
 """Autotuner for the batched kernel: per size class, time every kernel variant
-(block edge / register tile) on synthetic graphs of that class and keep the
-fastest.
+on synthetic graphs of that class and keep the fastest.
 
 The batched launch solves graphs of several size classes at once; each class
-may use a different variant (variant 0: 128 x 128 blocks with 8 x 8 register
-tiles; variant 1: 64 x 64 blocks with 4 x 4 tiles).  Choices are cached per
-device name in a JSON file and applied with :func:`apply_cached`.
+may use a different variant.  Both variants run 64 x 64 blocks with 4 x 4
+register tiles and differ in how the path matrix is produced: variant 0
+recovers each improved output's first argmin from the operands after a block
+product (lazy), variant 1 keeps the index of the last k-pair that lowered the
+accumulator inside the loop (eager).  Choices are cached per device name in a
+JSON file and applied with :func:`apply_cached`.
 
 Timing only: every variant computes the same distances (bit-exact on integer
 weights), so the choice never changes results on integer inputs.
