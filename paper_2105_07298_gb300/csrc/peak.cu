@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) peak_kernel(float *out, unsigned long lon
 
 }  // namespace apsp
 
-// Runs the relaxation loop (dtype_bytes 4: FP32 pair; 8: FP64 interval pair)
+// Runs the relaxation loop (dtype_bytes 4: FP32 pair; 8: the FP64 path's lower-bound pair)
 // on every SM and writes the achieved relaxations per clock per SM.  Uses the
 // caller's stream; synchronises it.  Scratch comes from stream-ordered
 // allocation and is freed before returning.
