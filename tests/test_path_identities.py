@@ -1,0 +1,101 @@
+"""The identities the kernels' path tracking rests on, checked on CPU.
+
+For one output, the sequential loop of Algorithm 1 (ascending k, strict "<")
+walks candidates c_0, c_1, ... from an initial value and records the k of each
+strict improvement; P is the last one.  The kernels get the same k in other
+ways:
+  * lazy recovery (phase 4, phase 1): the first k whose candidate equals the
+    final value, when that value is below the initial one;
+  * eager per-pair tracking (phase 4 early rounds, batched): a three-input
+    min folds the candidates of k-pairs (2p, 2p+1); the pair p of the last
+    strict decrease is kept, and inside it the lower k is taken if its
+    candidate equals the final value, else the upper one.
+FP64 pass 1 tests "x below ru(d)" for a float x and a double d; that equals
+"x below d" (a float below d is below the smallest float >= d).
+"""
+import math
+import random
+import struct
+
+import numpy as np
+import pytest
+
+
+def sequential(init, cands):
+    d, last = init, -1
+    for k, c in enumerate(cands):
+        if c < d:
+            d, last = c, k
+    return d, last
+
+
+def lazy(init, cands):
+    g = min([init] + list(cands))
+    if not g < init:
+        return g, -1
+    return g, next(k for k, c in enumerate(cands) if c == g)
+
+
+def eager_pairs(init, cands):
+    cs = list(cands) + ([math.inf] if len(cands) % 2 else [])
+    acc, kp = init, -1
+    for p in range(len(cs) // 2):
+        m = min(acc, cs[2 * p], cs[2 * p + 1])
+        if m < acc:
+            kp = p
+        acc = m
+    if kp < 0:
+        return acc, -1
+    return acc, 2 * kp if cs[2 * kp] == acc else 2 * kp + 1
+
+
+def _cases(seed, count):
+    rng = random.Random(seed)
+    for _ in range(count):
+        n = rng.randint(0, 40)
+        kind = rng.choice(["int", "small", "real"])
+        if kind == "int":      # many ties
+            cands = [float(rng.randint(0, 6)) for _ in range(n)]
+            init = float(rng.randint(0, 8))
+        elif kind == "small":  # few distinct values and +inf
+            cands = [rng.choice([1.0, 2.0, 3.0, math.inf]) for _ in range(n)]
+            init = rng.choice([2.0, 5.0, math.inf])
+        else:
+            cands = [rng.uniform(0, 10) for _ in range(n)]
+            init = rng.choice([rng.uniform(0, 10), math.inf])
+        yield init, cands
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_lazy_and_eager_pairs_give_the_sequential_path_entry(seed):
+    for init, cands in _cases(seed, 3000):
+        want = sequential(init, cands)
+        assert lazy(init, cands) == want, (init, cands)
+        assert eager_pairs(init, cands) == want, (init, cands)
+
+
+def _f32(x):
+    return struct.unpack("<f", struct.pack("<f", x))[0]
+
+
+def _ru32(d):
+    """Smallest float >= d (numpy rounding to float32 then one step up if below)."""
+    f = np.float32(d)
+    if float(f) < d:
+        f = np.nextafter(f, np.float32(np.inf))
+    return float(f)
+
+
+def test_float_below_double_equals_float_below_its_upper_float_bound():
+    rng = random.Random(5)
+    vals = [0.0, -0.0, 1.0, -1.0, 1e-40, 3e38, math.inf, -math.inf]
+    for _ in range(20000):
+        d = rng.choice([rng.uniform(-1e6, 1e6), rng.uniform(-1, 1) * 1e-30, rng.uniform(0, 100)])
+        x = _f32(d + rng.choice([0.0, 1e-9, -1e-9, 1.0, -1.0]) * rng.random())
+        vals.append(d)
+        assert (x < _ru32(d)) == (x < d), (x, d)
+    for d in vals:
+        for x in (_f32(d) if math.isfinite(d) else d, 0.0, 1.0, -1.0):
+            if math.isnan(x) or math.isnan(d):
+                continue
+            assert (x < _ru32(d)) == (x < d), (x, d)
