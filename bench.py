@@ -185,8 +185,11 @@ def kernel_source_hash() -> str:
 
 
 def profiled_traffic(n: int):
-    """dram bytes of phase 4 per round (its one or two launches) from the
-    committed ncu summary, if it was taken on the current kernel source (else None)."""
+    """DRAM bytes of phase 4 per round (its one or two launches) at size n, from
+    the committed ncu summary: measured on a small case (sampled rounds of an
+    n = 16384 solve) and scaled to n by the per-round byte model written there
+    (bytes per round proportional to n^2).  Only while the summary was taken on
+    the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "phase3_minplus_f32_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -211,10 +214,10 @@ def phase3_relax_per_round(n: int, T: int) -> float:
 
 def workload_config(n: int, world: int, dtype: str = "f32") -> dict:
     prec = "FP64" if dtype == "f64" else "FP32"
-    return {"workload": f"blocked FW, one dense directed graph per GPU, n={n}, edge prob 0.5, "
-                        f"integer weights U[1,100], {prec} distances + int32 path matrix",
+    return {"workload": f"blocked FW, dense directed graph n={n}, p=0.5, int weights U[1,100], "
+                        f"{prec} D + int32 P",
             "n": n, "edge_prob": 0.5, "path_matrix": True,
-            "l2": "inputs larger than L2 (4 GiB distances restored from a resident copy each step)",
+            "l2": "inputs > L2 (D restored from a resident copy each step)",
             "parallelism": f"{world} independent graph(s), one per GPU"}
 
 
@@ -361,7 +364,8 @@ def bench_fp64(torch, apsp, graphgen, args, dev):
         D.copy_(W)
         apsp.apsp_fw_f64(D, P)
 
-    step()  # warm-up
+    for _ in range(args.fp64_warmup):
+        step()
     torch.cuda.synchronize()
     apsp.profile_enable(True)
     t = time_events(torch, step, args.fp64_steps)
@@ -421,8 +425,11 @@ def bench_batched(torch, apsp, graphgen, args, dev):
     t_pg = time_events(torch, per_graph, 1)
     relax = float(np.sum(sizes.astype(np.float64) ** 3))
     plan.close()
+    facts = device_facts(torch)
+    peak = alu_peak_relax_per_s(facts["sms"], float(measured_peaks().get("sm_max_mhz", 2070.0)))
     return {"graphs": 4096, "n_range": [16, 512], "edge_prob": 0.3, "cuda_graph": True,
             "graphs_per_s": 4096 / t_solve, "ms": 1e3 * t_solve, "relax_per_s": relax / t_solve,
+            "frac_of_unit_peak": relax / t_solve / peak,
             "per_graph_launches": {"graphs_per_s": 4096 / t_pg, "ms": 1e3 * t_pg},
             "speedup_vs_per_graph": t_pg / t_solve,
             "autotuned_variants": {str(c): {"variant": r["variant"], "bounds": r["bounds"],
@@ -592,7 +599,7 @@ def run_ours(args):
         rate_meas = None
     traffic = profiled_traffic(n)
     launches = sum(c for _, c in prof.values())
-    phase_share = {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items()}
+    phase_share = {k: {"ms": round(v[0], 2), "launches": v[1]} for k, v in prof.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -614,7 +621,7 @@ def run_ours(args):
                                                     if rate_meas else None)},
         "phase_time_ms": phase_share,
         "gpu_launches": launches,
-        "clocks": clocks,
+        "clocks": ({k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")} if clocks else None),
         # the paper's Table 3 metric: Eq. 1 GFLOPS (2 per relaxation) per watt of
         # board power sampled during the timed region
         "energy": ({"power_w_mean": clocks["power_w_mean"],
@@ -624,12 +631,13 @@ def run_ours(args):
         "device": facts,
     }
 
+    details = {}
     if rank == 0 and not args.no_extras and args.dtype == "f32":
         del D
         torch.cuda.empty_cache()
         e2e_value, h2d, d2h, Wh, parts = bench_e2e(torch, apsp, graphgen, W, args)
         line["e2e"] = {"value": e2e_value * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "parts_ms": parts}
+                       "d2h_bytes_per_step": d2h, "parts_ms": {k: round(v, 2) for k, v in parts.items()}}
         del W, P
         torch.cuda.empty_cache()
         if args.fp64_n > 0:
@@ -638,31 +646,95 @@ def run_ours(args):
             T64 = apsp.block_size(torch.float64)
             p4_rate = phase3_relax_per_round(n64, T64) * ((n64 + T64 - 1) // T64) / (k3[0] / 1e3 / args.fp64_steps)
             rate64 = apsp.measure_peak(8)  # the lower-bound pair on registers (relax/clk/SM)
-            line["fp64"] = {"n": n64, "value": n64 ** 3 / t64, "unit": UNIT, "ms": 1e3 * t64,
-                            "path_matrix": True, "steps": args.fp64_steps,
-                            "phase_time_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof64.items()},
-                            "phase3_relax_per_s": p4_rate,
-                            "phase3_frac_of_unit_peak": p4_rate / alu_peak_relax_per_s(facts["sms"], max_mhz),
-                            "measured_pair_rate_relax_per_clk_sm": rate64,
-                            "phase3_frac_of_measured_pair_rate": p4_rate / (rate64 * facts["sms"] * max_mhz * 1e6)}
+            details["fp64"] = {"n": n64, "value": n64 ** 3 / t64, "unit": UNIT, "ms": 1e3 * t64,
+                               "path_matrix": True, "steps": args.fp64_steps, "warmup": args.fp64_warmup,
+                               "phase_time_ms": {k: {"ms": v[0], "launches": v[1]} for k, v in prof64.items()},
+                               "phase3_relax_per_s": p4_rate,
+                               "phase3_frac_of_unit_peak": p4_rate / alu_peak_relax_per_s(facts["sms"], max_mhz),
+                               "measured_pair_rate_relax_per_clk_sm": rate64,
+                               "phase3_frac_of_measured_pair_rate": p4_rate / (rate64 * facts["sms"] * max_mhz * 1e6)}
         torch.cuda.empty_cache()
-        line["batched"] = bench_batched(torch, apsp, graphgen, args, dev)
+        details["batched"] = bench_batched(torch, apsp, graphgen, args, dev)
         torch.cuda.empty_cache()
-        line["fwd_bwd"] = bench_fwd_bwd(torch, apsp, graphgen, args, dev)
+        details["fwd_bwd"] = bench_fwd_bwd(torch, apsp, graphgen, args, dev)
         torch.cuda.empty_cache()
         if args.sweep:
-            line["sweep"] = bench_sweep(torch, apsp, graphgen, args, dev, rate_meas)
+            details["sweep"] = bench_sweep(torch, apsp, graphgen, args, dev, rate_meas)
         # CPU baseline: the oracle as it stands, bounded prefix of the same graph
         rate, k, thr, tcpu = oracle_partial_rate(Wh.numpy(), args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"outer k iterations 0..{k - 1} of classic FW (Algorithm 1, "
-                                          f"FP32 + path) on the same n={n} graph, {tcpu:.1f} s "
-                                          "(fixed per-call cost excluded)"}
+                                "sample": f"first {k} outer k iterations of classic FW (Algorithm 1, FP32 + P) on the "
+                                          f"n={n} graph, {tcpu:.1f} s; prefix rate (early k improve more entries)"}
+        if args.cpu_full:
+            details["cpu_full_runs"] = oracle_full_runs(args.cpu_full)
+        for key, val in details.items():  # long records first, one line each
+            print("# detail " + json.dumps({key: val}), flush=True)
+        line["summary"] = summary_of(details, line)
     elif rank != 0:
         del W, D, P
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print("# detail " + json.dumps({"roofline": line["roofline"], "phase_time_ms": line.pop("phase_time_ms"),
+                                        "device": line.pop("device")}), flush=True)
+        print(json.dumps(compact_line(line)), flush=True)
     barrier(world)
+
+
+ROOFLINE_KEYS = ("bound", "achieved", "peak", "unit", "frac", "traffic", "frac_of_measured_pair_rate",
+                 "avg_round_ms")
+
+
+def compact_line(line):
+    """The final JSON line: the contract's keys plus short roofline, e2e,
+    cpu_baseline and summary objects (the long records are printed before it)."""
+    def r4(v):
+        return float("%.4g" % v) if isinstance(v, float) else v
+    out = dict(line)
+    out["roofline"] = {k: r4(line["roofline"][k]) for k in ROOFLINE_KEYS if k in line["roofline"]}
+    if out.get("energy"):
+        out["energy"] = {k: r4(v) for k, v in out["energy"].items() if k != "relax_per_joule"}
+    out["ms_per_step"] = round(out["ms_per_step"], 3)
+    return out
+
+
+def oracle_full_runs(sizes):
+    """Whole classic-FW solves by the CPU oracle (FP32 + path matrix) at small n,
+    beside the GPU sweep: relax/s of a complete run, no prefix."""
+    import oracle
+    import graphgen
+    out = []
+    for n in sizes:
+        W = graphgen.dense_graph(n, 0.5, SEED)
+        t0 = time.perf_counter()
+        oracle.fw(W, with_path=True)
+        t = time.perf_counter() - t0
+        out.append({"n": n, "s": t, "relax_per_s": float(n) ** 3 / t, "cores": oracle.num_threads()})
+    return out
+
+
+def summary_of(details, line):
+    """The headline numbers of the side measurements, short enough for the final line."""
+    out = {}
+    f = details.get("fp64")
+    if f:
+        out["fp64"] = {"value": float("%.4g" % f["value"]), "ms": round(f["ms"], 1),
+                       "phase3_frac": round(f["phase3_frac_of_unit_peak"], 4),
+                       "phase3_frac_of_pair": round(f["phase3_frac_of_measured_pair_rate"], 4)}
+    b = details.get("batched")
+    if b:
+        out["batched"] = {"graphs_per_s": round(b["graphs_per_s"]), "ms": round(b["ms"], 3),
+                          "relax_per_s": float("%.4g" % b["relax_per_s"]), "frac": round(b["frac_of_unit_peak"], 4),
+                          "vs_per_graph": round(b["speedup_vs_per_graph"], 1)}
+    fb = details.get("fwd_bwd")
+    if fb:
+        out["fwd_bwd_ms"] = round(fb["fwd_bwd_ms"], 3)
+        out["fwd_bwd_per_graph_ms"] = round(fb["per_graph_path"]["fwd_bwd_ms"], 2)
+    sw = details.get("sweep")
+    if sw:
+        out["sweep_relax_per_s"] = {str(p["n"]): float("%.4g" % p["with_path"]["relax_per_s"]) for p in sw["points"]}
+    en = line.get("energy")
+    if en:
+        out["eq1_gflops_per_w"] = round(en["eq1_gflops_per_w"], 2)
+    return out
 
 
 def main():
@@ -677,7 +749,10 @@ def main():
                     help="precision of the timed single-graph solve (the headline is f32)")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--fp64-n", type=int, default=32768)
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-warmup", type=int, default=3)
+    ap.add_argument("--cpu-full", type=lambda x: [int(v) for v in x.split(",") if v], default=[4096, 8192],
+                    help="sizes at which the CPU oracle runs a whole solve (empty: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--gpu-index", default=None)

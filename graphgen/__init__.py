@@ -12,9 +12,11 @@ Algorithm 1: a dense N x N distance matrix, infinity where there is no edge).
 
 Randomness is counter based: every element (i, j) of graph ``seed`` gets two
 32-bit hashes of its linear index ``e = i * n + j`` (MurmurHash3's 32-bit
-finaliser, Appleby 2011, applied to ``e`` xor a per-stream key).  The numpy and
-the torch implementations below compute the same integers, so a matrix drawn
-on the GPU for a large benchmark equals the one numpy draws on the host.
+finaliser, Appleby 2011, applied to ``lo32(e) xor fmix(hi32(e))`` xor a
+per-stream key; fmix(0) = 0, so below 2^32 elements this is ``e`` xor the key).
+The numpy and the torch implementations below compute the same integers, so a
+matrix drawn on the GPU for a large benchmark equals the one numpy draws on
+the host.
 
 * edge present   <=>  h_edge < round(p * 2**32)
 * integer weight  =   lo + h_weight mod (hi - lo + 1)
@@ -49,6 +51,12 @@ def _fmix32_int(h: int) -> int:
     return h
 
 
+def _index_word_np(e: np.ndarray) -> np.ndarray:
+    """32-bit word hashed for linear index e (uint64): lo32(e) xor fmix(hi32(e))."""
+    e = e.astype(np.uint64)
+    return (e & np.uint64(_M32)) ^ _fmix32_np(e >> np.uint64(32))
+
+
 def stream_keys(seed: int) -> tuple[int, int]:
     """The two 32-bit keys (edge stream, weight stream) of graph ``seed``."""
     s = int(seed) & _M32
@@ -56,8 +64,8 @@ def stream_keys(seed: int) -> tuple[int, int]:
 
 
 def _check_size(n: int) -> None:
-    if n < 0 or n * n > (1 << 32):
-        raise ValueError(f"n={n}: linear element index must fit in 32 bits (n <= 65536)")
+    if n < 0 or n > (1 << 31):
+        raise ValueError(f"n={n}: out of range")
 
 
 def dense_graph(n: int, p: float, seed: int, *, weights: str = "int", lo: float = 1,
@@ -69,7 +77,7 @@ def dense_graph(n: int, p: float, seed: int, *, weights: str = "int", lo: float 
     """
     _check_size(n)
     ke, kw = stream_keys(seed)
-    e = np.arange(n * n, dtype=np.uint64)
+    e = _index_word_np(np.arange(n * n, dtype=np.uint64))
     he = _fmix32_np(e ^ np.uint64(ke))
     hw = _fmix32_np(e ^ np.uint64(kw))
     thr = np.uint64(min(int(round(p * 2.0 ** 32)), 1 << 32))
@@ -84,6 +92,51 @@ def dense_graph(n: int, p: float, seed: int, *, weights: str = "int", lo: float 
     out = np.where(present, w, np.inf).astype(dtype).reshape(n, n)
     np.fill_diagonal(out, 0)
     return out
+
+
+def _torch_fmix(torch, device):
+    M = torch.tensor(_M32, dtype=torch.int64, device=device)
+
+    def fmix(h):
+        h = h & M
+        h = h ^ (h >> 16)
+        h = (h * _C1) & M
+        h = h ^ (h >> 13)
+        h = (h * _C2) & M
+        h = h ^ (h >> 16)
+        return h
+    return fmix, M
+
+
+def dense_graph_rows_torch(n: int, r0: int, r1: int, p: float, seed: int, *, weights: str = "int",
+                           lo: float = 1, hi: float = 100, dtype=None, device="cpu"):
+    """Rows r0..r1-1 of the matrix :func:`dense_graph` draws (same values), as an
+    (r1 - r0, n) torch tensor on ``device``."""
+    import torch
+
+    _check_size(n)
+    dtype = dtype or torch.float32
+    ke, kw = stream_keys(seed)
+    thr = min(int(round(p * 2.0 ** 32)), 1 << 32)
+    fmix, M = _torch_fmix(torch, device)
+    cols = torch.arange(n, dtype=torch.int64, device=device)
+    rows = torch.arange(r0, r1, dtype=torch.int64, device=device)
+    e = rows[:, None] * n + cols[None, :]
+    e = (e & M) ^ fmix(e >> 32)
+    he = fmix(e ^ ke)
+    hw = fmix(e ^ kw)
+    del e
+    if weights == "int":
+        w = float(lo) + (hw % (int(hi) - int(lo) + 1)).to(torch.float64)
+    elif weights == "real":
+        w = float(lo) + (float(hi) - float(lo)) * (hw.to(torch.float64) / 2.0 ** 32)
+    else:
+        raise ValueError(weights)
+    w = torch.where(he < thr, w, torch.full_like(w, float("inf")))
+    blk = w.to(dtype)
+    idx = torch.arange(r0, r1, device=device)
+    blk[idx - r0, idx] = 0
+    return blk
 
 
 def dense_graph_torch(n: int, p: float, seed: int, *, weights: str = "int", lo: float = 1,
@@ -101,38 +154,11 @@ def dense_graph_torch(n: int, p: float, seed: int, *, weights: str = "int", lo: 
     ld = ld or n
     if out is None:
         out = torch.empty((n, ld), dtype=dtype, device=device)
-    ke, kw = stream_keys(seed)
-    thr = min(int(round(p * 2.0 ** 32)), 1 << 32)
-    M = torch.tensor(_M32, dtype=torch.int64, device=device)
-
-    def fmix(h):
-        h = h & M
-        h = h ^ (h >> 16)
-        h = (h * _C1) & M
-        h = h ^ (h >> 13)
-        h = (h * _C2) & M
-        h = h ^ (h >> 16)
-        return h
-
-    cols = torch.arange(n, dtype=torch.int64, device=device)
+    rows_per_chunk = max(1, min(rows_per_chunk, (1 << 27) // max(n, 1)))
     for r0 in range(0, n, rows_per_chunk):
         r1 = min(n, r0 + rows_per_chunk)
-        rows = torch.arange(r0, r1, dtype=torch.int64, device=device)
-        e = rows[:, None] * n + cols[None, :]
-        he = fmix(e ^ ke)
-        hw = fmix(e ^ kw)
-        if weights == "int":
-            w = float(lo) + (hw % (int(hi) - int(lo) + 1)).to(torch.float64)
-        elif weights == "real":
-            w = float(lo) + (float(hi) - float(lo)) * (hw.to(torch.float64) / 2.0 ** 32)
-        else:
-            raise ValueError(weights)
-        w = torch.where(he < thr, w, torch.full_like(w, float("inf")))
-        blk = w.to(dtype)
-        idx = torch.arange(r0, r1, device=device)
-        blk[idx - r0, idx] = 0
-        out[r0:r1, :n] = blk
-        del e, he, hw, w, blk
+        out[r0:r1, :n] = dense_graph_rows_torch(n, r0, r1, p, seed, weights=weights, lo=lo, hi=hi,
+                                                dtype=dtype, device=device)
     if ld > n:
         out[:, n:] = float("nan")  # padding columns: never read by a correct kernel
     return out

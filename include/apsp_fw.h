@@ -31,8 +31,13 @@
  *  - Every entry point returns an apsp_status (int).
  *  - Results: on integer-valued weights every sum is exact (|D| < 2^24 in
  *    FP32, < 2^53 in FP64), so D is bit-exact with any correct algorithm.
- *    On real weights D and P are bit-exact with a sequential blocked FW of
- *    the same block size (apsp_fw_block_size) on the same precision.
+ *    On real weights apsp_fw_f32 and apsp_fw_f64 are bit-exact (D and P) with
+ *    a sequential blocked FW of the same block size (apsp_fw_block_size) in
+ *    the same precision: every candidate sum is rounded once, in the
+ *    paper's phase and k order.  The batched entry points compute phases 2/3
+ *    as one product with the closed diagonal block instead (equal in exact
+ *    arithmetic), so on real weights they are held to a relative error
+ *    bound (about path length x 2^-24) rather than bit-exactness.
  */
 #ifndef APSP_FW_H
 #define APSP_FW_H
@@ -49,7 +54,9 @@ typedef enum {
   APSP_ECUDA = 2,         /* a CUDA call or launch failed */
   APSP_ENOMEM = 3,        /* device scratch allocation failed */
   APSP_EUNSUPPORTED = 4,  /* size or feature outside what this build supports */
-  APSP_ETOODEEP = 5       /* backward: a path's recursion exceeded the walk stack */
+  APSP_ETOODEEP = 5,      /* backward: a path's recursion exceeded the walk stack */
+  APSP_ENEGCYCLE = 6,     /* apsp_check_negative_cycle: some D[i][i] < 0 */
+  APSP_ETIMEOUT = 7       /* a kernel's bounded wait for an asynchronous copy ran out */
 } apsp_status;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -95,9 +102,10 @@ int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *st
  * launch.  Graph g has n_g vertices and occupies n_g * n_g consecutive
  * elements (row-major, ld = n_g) starting at element offset off[g] of the
  * packed buffers.  Every graph is solved with the same relaxation rule as
- * above; results are bit-exact with the single-graph path on integer weights
- * (and with a blocked FW of the block size of the graph's size class on real
- * weights).
+ * above; results are bit-exact with the single-graph path on integer weights.
+ * On real weights phases 2/3 of a graph are one min-plus product with its
+ * closed diagonal block (rounded differently from the sequential k loop), and
+ * D stays within the FP32 error bound of the exact distances.
  *
  * Planning splits the graphs into size classes, orders them largest first
  * (longest-processing-time order) and uploads the work list.  A plan holds
@@ -135,9 +143,10 @@ int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_t *h_n, cons
  * APSP_EUNSUPPORTED before anything is enqueued.  Arguments and results are
  * those of apsp_fw_batched_f32 (same kernels, same results).
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture on the device.  Every call shares the
+ * Every call looks up the array's device address (cudaGetSymbolAddress, with
+ * the caller's device current; this allocates nothing).  The first call on a
+ * device also loads the library's module there: make that first call before
+ * any stream capture on the device.  Every call shares the
  * array and it keeps the last call's contents (each call resets what must
  * start at zero); calls that overlap on the GPU (different streams or host
  * threads) race on it, so the caller must serialise them.  h_n and h_off are
@@ -183,6 +192,22 @@ int apsp_fw_backward_f32(const float *d_grad_dist, const int32_t *d_path, const 
                          float *d_grad_w, int64_t n, int64_t ld, int64_t batch, int64_t stride,
                          int32_t *d_status, void *stream);
 
+/* The same backward pass for a packed batch of uneven graphs, in the layout
+ * of the batched forward: graph g has d_n[g] vertices and occupies
+ * d_n[g]^2 consecutive elements (row-major, ld = d_n[g]) at element offset
+ * d_off[g] of every packed buffer (gradient, P, D and the output).
+ *   d_n, d_off : DEVICE arrays of num_graphs entries (int32, int64); graphs
+ *                must not overlap.  A graph with d_n[g] <= 0 is skipped
+ *                (d_n[g] < 0 also reports APSP_EINVAL in *d_status).
+ *   d_grad_w   : fully written over every graph's region (zero on the
+ *                diagonal, non-edges and unused edges); gaps between graphs
+ *                are not touched.
+ *   d_status   : optional device int32, as for apsp_fw_backward_f32.
+ * Returns APSP_EINVAL for num_graphs < 0 or a NULL buffer with num_graphs > 0. */
+int apsp_fw_backward_packed_f32(const float *d_grad_dist, const int32_t *d_path, const float *d_dist,
+                                float *d_grad_w, const int32_t *d_n, const int64_t *d_off,
+                                int32_t num_graphs, int32_t *d_status, void *stream);
+
 
 /* ------------------------------------------------------------------------
  * Phase timing (a measurement hook; the paper times whole runs only, §4.1).
@@ -207,11 +232,32 @@ int apsp_profile_enable(int on);
  * dtype_bytes or a NULL output. */
 int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm, void *stream);
 
-/* Synchronizes `stream`, then returns and clears the error word that the
+/* Synchronizes `stream`, then returns and clears the error words that the
  * single-graph kernels set on the device when one of their bounded waits for
- * an asynchronous copy runs out (the kernel then leaves its block unchanged):
- * APSP_OK if no wait ran out since the last call, else APSP_ECUDA. */
+ * an asynchronous copy runs out (the kernel then leaves its block unchanged,
+ * so the result of that solve is incomplete): APSP_OK if no wait ran out
+ * since the last call, APSP_ETIMEOUT if one did, APSP_ECUDA if the stream or
+ * the read-back failed. */
 int apsp_device_status(void *stream);
+
+/* Self-test of that timeout path (a test hook; the paper has no counterpart).
+ * Enqueues on `stream` one small kernel that waits, with the bounded mbarrier
+ * wait of the bulk-copy kernels, on a barrier that nothing completes; after
+ * `polls` polls (1 .. 2^22) the wait gives up and the kernel records
+ * APSP_ETIMEOUT exactly as a product kernel would, then returns.  Nothing
+ * faults and the context stays usable: the next apsp_device_status returns
+ * APSP_ETIMEOUT and clears it.  Returns APSP_EINVAL for polls out of range. */
+int apsp_wait_timeout_selftest(uint32_t polls, void *stream);
+
+/* Negative-cycle check of a solved matrix (§2.2 assumes no negative cycle;
+ * Floyd-Warshall leaves D[i][i] < 0 on every vertex of one).  Scans the
+ * diagonal of the n x n matrix d_dist (elem_bytes 4: float, 8: double; leading
+ * dimension ld) after the work already on `stream`, synchronizes `stream`, and
+ * returns APSP_ENEGCYCLE if some D[i][i] < 0, else APSP_OK.  With a negative
+ * cycle the other distances and P are not meaningful.  Uses one fixed device
+ * word of the library (calls from several host threads are serialised by a
+ * lock); allocates nothing; not for use while `stream` is being captured. */
+int apsp_check_negative_cycle(const void *d_dist, int elem_bytes, int64_t n, int64_t ld, void *stream);
 int apsp_profile_collect(double *ms, int64_t *launches);
 
 /* The same records one by one, in launch order (per-round timing: the r-th

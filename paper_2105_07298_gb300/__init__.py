@@ -19,7 +19,8 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libapspfw.so")
 
-APSP_OK, APSP_EINVAL, APSP_ECUDA, APSP_ENOMEM, APSP_EUNSUPPORTED, APSP_ETOODEEP = range(6)
+(APSP_OK, APSP_EINVAL, APSP_ECUDA, APSP_ENOMEM, APSP_EUNSUPPORTED, APSP_ETOODEEP, APSP_ENEGCYCLE,
+ APSP_ETIMEOUT) = range(8)
 
 # Every symbol include/apsp_fw.h declares, with its ctypes signature.
 _i32, _i64, _p = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
@@ -40,6 +41,9 @@ SIGNATURES = {
     "apsp_batched_set_variant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "apsp_batched_get_variant": (ctypes.c_int, [ctypes.c_int]),
     "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
+    "apsp_fw_backward_packed_f32": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _i32, _p, _p]),
+    "apsp_check_negative_cycle": (ctypes.c_int, [_p, ctypes.c_int, _i64, _i64, _p]),
+    "apsp_wait_timeout_selftest": (ctypes.c_int, [ctypes.c_uint32, _p]),
     "apsp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "apsp_device_status": (ctypes.c_int, [_p]),
     "apsp_measure_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _p]),
@@ -150,6 +154,23 @@ def device_status(stream=None) -> int:
     return int(load().apsp_device_status(_stream_ptr(stream)))
 
 
+def wait_timeout_selftest(polls: int = 4096, stream=None):
+    """Enqueue the bounded-wait self-test kernel (its wait runs out; see apsp_fw.h)."""
+    _check(load().apsp_wait_timeout_selftest(int(polls), _stream_ptr(stream)), "apsp_wait_timeout_selftest")
+
+
+def check_negative_cycle(dist, stream=None) -> bool:
+    """True if the solved CUDA matrix ``dist`` has a negative diagonal entry (a
+    negative cycle in the input).  Synchronizes the stream."""
+    import torch
+    ptr, n, ld = _matrix_args(dist, dist.dtype if dist.dtype in (torch.float32, torch.float64) else torch.float32)
+    st = load().apsp_check_negative_cycle(ptr, dist.element_size(), n, ld, _stream_ptr(stream))
+    if st == APSP_ENEGCYCLE:
+        return True
+    _check(st, "apsp_check_negative_cycle")
+    return False
+
+
 def measure_peak(dtype_bytes: int = 4, stream=None) -> float:
     """Relaxations per clock per SM the inner-loop instruction pair sustains on this GPU."""
     out = ctypes.c_double()
@@ -186,10 +207,12 @@ def profile_records() -> list:
 
 
 from .batched import BatchedPlan, apsp_fw_batched_f32, apsp_fw_batched  # noqa: E402
-from .backward import apsp_fw_backward_f32, ShortestPathDistances, shortest_path_distances  # noqa: E402
+from .backward import (apsp_fw_backward_f32, apsp_fw_backward_packed_f32, ShortestPathDistances,  # noqa: E402
+                       shortest_path_distances, shortest_path_distances_packed)
 
 __all__ = [
     "load", "ApspError", "block_size", "apsp_fw_f32", "apsp_fw_f64", "apsp_fw",
     "BatchedPlan", "apsp_fw_batched_f32", "apsp_fw_batched", "apsp_fw_backward_f32",
-    "ShortestPathDistances", "shortest_path_distances",
+    "apsp_fw_backward_packed_f32", "ShortestPathDistances", "shortest_path_distances",
+    "shortest_path_distances_packed", "check_negative_cycle", "wait_timeout_selftest",
 ]

@@ -9,6 +9,8 @@ import ctypes
 
 import numpy as np
 
+MAX_N = 1024  # largest graph the batched kernel takes (apsp_batched_class_bounds)
+
 
 def _host_arrays(sizes, offsets):
     n = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))

@@ -4,9 +4,13 @@
 // A copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
 // global to shared memory completes on an mbarrier as transaction bytes.
 // Every wait is bounded: after kWaitLimit polls it reports failure, and the
-// caller records an error and leaves instead of spinning forever.
+// caller records APSP_ETIMEOUT in the translation unit's error word
+// (report_wait_timeout) and leaves instead of spinning forever.
 #pragma once
+#include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "../../include/apsp_fw.h"
 
 namespace apsp {
 
@@ -15,6 +19,19 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 // Error word the kernels of a translation unit set when a bounded wait runs
 // out (read back by apsp_device_status).
 static __device__ int g_device_error = 0;
+
+// Records that a bounded wait ran out (any thread may call it).
+__device__ __forceinline__ void report_wait_timeout() { atomicExch(&g_device_error, APSP_ETIMEOUT); }
+
+// Host side: returns and clears this translation unit's error word (APSP_OK if
+// no wait ran out since the last call; APSP_ECUDA if the copy itself failed).
+static inline int take_tu_device_error() {
+  int v = 0;
+  const int zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
+  if (v != 0 && cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
+  return v;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -61,9 +78,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Waits for phase `parity` of `bar` to complete; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it)
+// Waits for phase `parity` of `bar` to complete; false if `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -484,8 +484,10 @@ APSP_EXPORT int apsp_batched_get_variant(int cls) {
 // The array (1 MiB + 16 bytes, up to kNoAllocMaxGraphs graphs) is held by
 // every GPU that loads the library until the process exits.  Host code cannot
 // pass the array's name to a kernel (in host code it is only a stand-in, not
-// a device address): the first call on each device looks its address up with
-// cudaGetSymbolAddress while that device is current and caches it.  All calls
+// a device address): every call looks its address up with
+// cudaGetSymbolAddress while the caller's device is current.  The first call
+// on a device also loads the library's module there, so it should come
+// before any stream capture on that device.  All calls
 // share the array and it keeps the previous call's contents; each call
 // resets the counter it needs.  Calls that overlap on the GPU (other streams,
 // other host threads) race on the array and must be serialised by the caller.
@@ -495,7 +497,6 @@ namespace apsp {
 constexpr int kNoAllocMaxGraphs = 65536;
 constexpr size_t kNoAllocBytes = 16 + (size_t)kNoAllocMaxGraphs * (4 + 4 + 8);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-static unsigned char *g_noalloc_addr[64];  // device address of g_noalloc_scratch, per device
 
 // One CTA: counting sort of the graphs by decreasing size (ties in any
 // order), each entry tagged with its class's variant; also resets the work
@@ -534,17 +535,15 @@ APSP_EXPORT int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, cons
   if (num > apsp::kNoAllocMaxGraphs) return APSP_EUNSUPPORTED;
   if (num == 0) return APSP_OK;
   if (!d_dist) return APSP_EINVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ECUDA;
-  if (!apsp::g_noalloc_addr[dev]) {
-    void *ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, apsp::g_noalloc_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return APSP_ECUDA;
-    }
-    apsp::g_noalloc_addr[dev] = static_cast<unsigned char *>(ptr);
+  // The array's device address on the current device, looked up on every call
+  // (cheap, allocates nothing) so that it stays right after a device reset
+  // reloads the module.  The first call on a device loads the module there.
+  void *ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, apsp::g_noalloc_scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return APSP_ECUDA;
   }
-  unsigned char *base = apsp::g_noalloc_addr[dev];
+  unsigned char *base = static_cast<unsigned char *>(ptr);
   int *d_counter = reinterpret_cast<int *>(base);
   int32_t *d_order = reinterpret_cast<int32_t *>(base + 16);
   int32_t *d_n = d_order + apsp::kNoAllocMaxGraphs;

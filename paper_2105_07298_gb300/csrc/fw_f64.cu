@@ -19,24 +19,21 @@
 //    first such k is the path entry; if none has, the candidates with
 //    lo <= min(ru(old), their up) are evaluated with a real FP64 add.
 //
-// Schedule per round r (TB = 128), the blocked FW of §2.2:
+// Schedule per round r (TB = 128), the blocked FW of §2.2, every phase in the
+// paper's k order:
 //  K1  fw64_diag         phase 1: Algorithm 1 on block (r,r), k sequential,
-//                        with the same interval filter per relaxation; also
-//                        packs the closed block as a product operand.
-//  K2a fw64_pack_panels  packs row blocks (r,J) and column blocks (I,r).
-//  K2b fw64_product<1,2> phases 2 and 3 as min-plus products with the closed
-//                        diagonal block: (r,J) <- min(C, D*(r,r) (x) C) and
-//                        (I,r) <- min(C, C (x) D*(r,r)) (the sequential k loop
-//                        over a panel block equals one product with the
-//                        closure); re-packs the updated blocks.
-//  K3  fw64_product<0>   phase 4: (I,J) <- min(C, D(I,r) (x) D(r,J)); rounds
+//                        with the interval filter per relaxation.
+//  K2  fw64_lines        phases 2 and 3: the row blocks (r,J) and column
+//                        blocks (I,r), k sequential per line with the same
+//                        filter; packs the finished blocks as phase-4 operands.
+//  K3  fw64_product      phase 4: (I,J) <- min(C, D(I,r) (x) D(r,J)); rounds
 //                        0-15 run an eager instance that also keeps, per
 //                        output, the k-pair where min lo last decreased.
 // As in the FP32 path, phase 4 of round r updates row and column r+1 first,
 // then the rest while K1/K2 of round r+1 run on a second stream.
-// On integer-valued weights all sums are exact and D equals every correct FW;
-// on real weights phases 2/3 round through the closure instead of a chain of
-// sums, within the same error bound (relative ~ path length x 2^-53).
+// Every candidate sum is one IEEE FP64 addition rounded to nearest, taken in
+// the order of the sequential blocked FW, so D and P are bit-exact with it on
+// any weights (and with every correct FW on integer-valued weights).
 #include <float.h>
 #include <stdint.h>
 
@@ -166,137 +163,236 @@ __device__ __forceinline__ void relax2_rm(float &acc, unsigned long long a, unsi
       : "l"(a), "l"(b));
 }
 
-// ---------------------------------------------------------------- packing
-// Packs a T x T block held in shared memory (row stride S, +inf padded) as
-// an A operand (as_b = false) or a B operand (as_b = true).
-template <int S>
-__device__ void pack_block(const double *s, Pack *pk, bool as_b) {
-  bool ex = true;
-  for (int e = threadIdx.x; e < T * T / 2; e += blockDim.x) {
-    const int kp = e / T, x = e % T;
-    const double v0 = as_b ? s[(2 * kp) * S + x] : s[x * S + 2 * kp];
-    const double v1 = as_b ? s[(2 * kp + 1) * S + x] : s[x * S + 2 * kp + 1];
-    pk->lo[x >> 6][kp][x & 63] = packf2(f64_down(v0), f64_down(v1));
-    pk->hi[x >> 6][kp][x & 63] = packf2(f64_up(v0), f64_up(v1));
-  }
-  for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
-    const int x = e / T, k = e % T;  // row x of the row-contiguous copies
-    const double v = as_b ? s[k * S + x] : s[x * S + k];
-    const float vl = f64_down(v), vh = f64_up(v);
-    pk->rlo[x][k] = vl;
-    pk->rhi[x][k] = vh;
-    pk->r64[x][k] = v;
-    ex = ex && vl == vh;
-  }
-  const int all = __syncthreads_and(ex);
-  if (threadIdx.x == 0) pk->exact = all;
-}
-
 // ---------------------------------------------------------------- K1
-// Phase 1 on block (r,r): Algorithm 1 (strict "<", k ascending).  Each
-// element keeps an upper float bound dhi beside it, and the lower bounds of
-// the pivot row and column are published per step, so a relaxation whose
-// lower bound rd(rd(d_ik) + rd(d_kj)) is not below dhi_ij is skipped without
-// an FP64 add (it cannot be an improvement).  The owners of row/column k+1
-// publish their lower bounds after their step-k update (one barrier per
-// step).  Then the closed block is packed as the A operand of the row-panel
-// products and the B operand of the column-panel products.
-constexpr int K1_THREADS = 1024;
+// Phase 1 on block (r,r): Algorithm 1 (strict "<", k ascending), k
+// sequential as the paper's phase 1.  The block's values live in shared
+// memory as doubles (d) with their lower float bounds (dlo = rd d); each
+// thread keeps the upper bounds (dhi = ru d) of its 4 x 8 elements in
+// registers.  At step k a candidate d[i][k] + d[k][j] is skipped without an
+// FP64 add when its lower bound rd(dlo[i][k] + dlo[k][j]) is not below dhi[i][j]
+// (then fl(d[i][k] + d[k][j]) >= d[i][j]); otherwise one FP64 add decides.
+// Step k never changes row or column k (D[k][k] = 0), so every thread reads
+// them straight from shared memory while the step writes other elements; one
+// barrier per step.  Element (i, j) of thread (ty, tx) = (tid / 16, tid % 16):
+// i = ty + 32 rr (rr 0..3), j = 2 tx + q + 32 cb (cb 0..3, q 0..1).
+// Also marks every operand pack of the round's set exact (the phase-2/3
+// kernel clears the flag of a pack holding a value that is not a float).
+constexpr int K1_THREADS = 512;
 struct K1Smem {
   double d[T * T];
-  float dhi[T * T];
-  float rlo[2][T];  // rd of row k of the block
-  float clo[2][T];  // rd of column k of the block
+  float dlo[T * T];
 };
 
-__global__ void __launch_bounds__(K1_THREADS)
-    fw64_diag(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r,
-              Pack *diagA, Pack *diagB) {
+__global__ void __launch_bounds__(K1_THREADS, 1)
+    fw64_diag(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R, Pack *packA,
+              Pack *packB) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   K1Smem &sm = *reinterpret_cast<K1Smem *>(smem_raw);
-  constexpr int EPT = T * T / K1_THREADS;
   const int base = r * T, m = min(T, n - base), tid = threadIdx.x;
+  const int ty = tid >> 4, tx = tid & 15;
   const double INF = inf<double>();
   for (int e = tid; e < T * T; e += K1_THREADS) {
     const int i = e / T, j = e % T;
     const double v = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : INF;
     sm.d[e] = v;
-    sm.dhi[e] = f64_up(v);
-    if (i == 0) sm.rlo[0][j] = f64_down(v);
-    if (j == 0) sm.clo[0][i] = f64_down(v);
+    sm.dlo[e] = f64_down(v);
   }
-  int pk[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; ++q) pk[q] = -1;
+  if (packA)
+    for (int b = tid; b < R; b += K1_THREADS) {
+      packA[b].exact = 1;
+      packB[b].exact = 1;
+    }
   __syncthreads();
-  for (int k = 0; k < m; ++k) {
-    const int buf = k & 1, nb = buf ^ 1;
+  float dhi[4][8];
+  unsigned pk[4][2];  // byte 4 (cb & 1) ... : block-local k of the last improvement, 0xFF none
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = tid + q * K1_THREADS;
-      const int i = e / T, j = e % T;
-      const float lo = __fadd_rd(sm.clo[buf][i], sm.rlo[buf][j]);
-      if (lo < sm.dhi[e]) {
-        const double cand = __dadd_rn(sm.d[i * T + k], sm.d[k * T + j]);
-        if (cand < sm.d[e]) {
-          sm.d[e] = cand;
-          sm.dhi[e] = f64_up(cand);
-          pk[q] = base + k;
+  for (int rr = 0; rr < 4; ++rr) {
+    pk[rr][0] = pk[rr][1] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) dhi[rr][c] = f64_up(sm.d[(ty + 32 * rr) * T + 2 * tx + (c & 1) + 32 * (c >> 1)]);
+  }
+#pragma unroll 1
+  for (int k = 0; k < m; ++k) {
+    float alo[4];
+    unsigned long long blo[4];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) alo[rr] = sm.dlo[(ty + 32 * rr) * T + k];
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb) blo[cb] = *reinterpret_cast<const unsigned long long *>(&sm.dlo[k * T + 2 * tx + 32 * cb]);
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const unsigned long long aa = packf2(alo[rr], alo[rr]);
+#pragma unroll
+      for (int cb = 0; cb < 4; ++cb) {
+        const float2 lo = sum2_rm(aa, blo[cb]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int c = 2 * cb + q;
+          if ((q ? lo.y : lo.x) < dhi[rr][c]) {
+            const int i = ty + 32 * rr, j = 2 * tx + q + 32 * cb;
+            const double cand = __dadd_rn(sm.d[i * T + k], sm.d[k * T + j]);
+            if (cand < sm.d[i * T + j]) {
+              sm.d[i * T + j] = cand;
+              sm.dlo[i * T + j] = f64_down(cand);
+              dhi[rr][c] = f64_up(cand);
+              pk[rr][cb >> 1] = __byte_perm(pk[rr][cb >> 1], (unsigned)k,
+                                            0x3210 ^ ((0x3210 & (0xF << (4 * (c & 3)))) ^ (4 << (4 * (c & 3)))));
+            }
+          }
         }
       }
-      if (i == k + 1) sm.rlo[nb][j] = f64_down(sm.d[e]);
-      if (j == k + 1) sm.clo[nb][i] = f64_down(sm.d[e]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < EPT; ++q) {
-    const int e = tid + q * K1_THREADS;
-    const int i = e / T, j = e % T;
-    if (i < m && j < m && pk[q] >= 0) {
-      const int64_t g = (int64_t)(base + i) * ld + base + j;
-      D[g] = sm.d[e];
-      if (P) P[g] = pk[q];
+  for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int i = ty + 32 * rr, j = 2 * tx + (c & 1) + 32 * (c >> 1);
+      const unsigned kl = (pk[rr][c >> 2] >> (8 * (c & 3))) & 0xFFu;
+      if (kl != 0xFFu && i < m && j < m) {
+        const int64_t g = (int64_t)(base + i) * ld + base + j;
+        D[g] = sm.d[i * T + j];
+        if (P) P[g] = base + (int)kl;
+      }
     }
-  }
-  if (diagA) {
-    pack_block<T>(sm.d, diagA, false);
-    pack_block<T>(sm.d, diagB, true);
-  }
 }
 
-// ---------------------------------------------------------------- K2a
-// Packs the round's row blocks (r,J) as B operands (packB[J]) and column
-// blocks (I,r) as A operands (packA[I]), before phases 2/3 update them.
-constexpr int K2A_THREADS = 512;
-__global__ void __launch_bounds__(K2A_THREADS)
-    fw64_pack_panels(const double *__restrict__ D, int64_t ld, int n, int r, int R, Pack *packA,
-                     Pack *packB) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  double *s = reinterpret_cast<double *>(smem_raw);
-  constexpr int S = T + 1;
-  const int b = blockIdx.x;
+// ---------------------------------------------------------------- K2
+// Phases 2 and 3, k sequential in the paper's order (as the FP32 path):
+// within a row block (r,J) every column j evolves on its own,
+//   own[i][j] <- min(own[i][j], diag[i][k] + own[k][j])   (k ascending),
+// within a column block (I,r) every row i does,
+//   own[i][j] <- min(own[i][j], own[i][k] + diag[k][j]),
+// with the diagonal block final after K1.  A warp keeps four such lines in
+// registers as doubles with their float bounds (lane l: positions 2l, 2l+1,
+// 2l+64, 2l+65).  At step k the lower bound of the pivot own[k] is broadcast
+// by a shuffle and paired with the diagonal's lower bounds from shared memory
+// (one add.rm.f32x2 per two candidates); only when some lane's candidate
+// lower bound is below its upper bound does the warp fetch the pivot's double
+// and run the exact FP64 adds.  Then the finished lines are written (D and P
+// where improved) and packed as phase-4 operands: a row block as the B
+// operand packB[J] (B[k][j] = own[k][j]), a column block as the A operand
+// packA[I] (A[i][k] = own[i][k]); in (line, position) terms both are
+// lo[line / 64][pos / 2][line % 64] = (rd at pos, rd at pos + 1), hi likewise
+// with ru, and rlo/rhi/r64[line][pos].  Entries outside the matrix are +inf.
+namespace k2 {
+constexpr int K2_THREADS = 256, LINES = 2, PARTS = T / (K2_THREADS / 32 * LINES), MS = T + 2;
+constexpr int SMEM = T * MS * 4;
+}  // namespace k2
+
+__global__ void __launch_bounds__(k2::K2_THREADS, 2)
+    fw64_lines(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R, Pack *packA,
+               Pack *packB) {
+  using namespace k2;
+  extern __shared__ __align__(16) float Mlo[];  // [T][MS]: Mlo[k][pos] = rd of the diagonal entry
+  const int b = blockIdx.x / PARTS, part = blockIdx.x % PARTS;
   const bool is_row = b < R - 1;
   int other = is_row ? b : b - (R - 1);
   other += (other >= r);
   const int base_r = r * T, m_r = min(T, n - base_r);
   const int base_o = other * T, m_o = min(T, n - base_o);
-  const int rows = is_row ? m_r : m_o, cols = is_row ? m_o : m_r;
-  const int64_t row0 = is_row ? base_r : base_o, col0 = is_row ? base_o : base_r;
-  for (int e = threadIdx.x; e < T * T; e += K2A_THREADS) {
-    const int i = e / T, j = e % T;
-    s[i * S + j] = (i < rows && j < cols) ? D[(row0 + i) * ld + col0 + j] : inf<double>();
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const double INF = inf<double>();
+  const double *diag = D + (int64_t)base_r * ld + base_r;
+  for (int e = tid; e < T * T; e += K2_THREADS) {
+    const int i = e / T, k = e % T;
+    const double x = (i < m_r && k < m_r) ? diag[(int64_t)i * ld + k] : INF;
+    Mlo[is_row ? k * MS + i : i * MS + k] = f64_down(x);  // Mlo[k][pos]
+  }
+  const int line0 = part * (T / PARTS) + w * LINES;
+  // Element (line, pos) of the own block sits at D[g0 + line * sl + pos * sp].
+  const int64_t g0 = is_row ? (int64_t)base_r * ld + base_o : (int64_t)base_o * ld + base_r;
+  const int64_t sl = is_row ? 1 : ld, sp = is_row ? ld : 1;
+  // the diagonal entry paired with position pos at step k: row block diag[pos][k], column block diag[k][pos]
+  const int64_t dpos = is_row ? ld : 1, dk = is_row ? 1 : ld;
+  double v[LINES][4];
+  float vlo[LINES][4], vhi[LINES][4];
+  unsigned pk[LINES];  // byte q: round-local k of the last improvement of slot q, 0xFF: none
+#pragma unroll
+  for (int c = 0; c < LINES; ++c) {
+    pk[c] = 0xFFFFFFFFu;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int line = line0 + c, pos = 2 * lane + (q & 1) + 64 * (q >> 1);
+      v[c][q] = (line < m_o && pos < m_r) ? D[g0 + line * sl + pos * sp] : INF;
+      vlo[c][q] = f64_down(v[c][q]);
+      vhi[c][q] = f64_up(v[c][q]);
+    }
   }
   __syncthreads();
-  pack_block<S>(s, is_row ? &packB[other] : &packA[other], is_row);
+  // Step k: owner lane (k mod 64) / 2, slot 2 (k / 64) + (k mod 2).
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll 1
+    for (int kk = 0; kk < 32; ++kk) {
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        const int k = 64 * h + 2 * kk + par;
+        const unsigned long long m01 = *reinterpret_cast<const unsigned long long *>(&Mlo[k * MS + 2 * lane]);
+        const unsigned long long m23 = *reinterpret_cast<const unsigned long long *>(&Mlo[k * MS + 64 + 2 * lane]);
+#pragma unroll
+        for (int c = 0; c < LINES; ++c) {
+          const float vk_lo = __shfl_sync(kFullMask, vlo[c][2 * h + par], kk);
+          const unsigned long long vv = packf2(vk_lo, vk_lo);
+          const float2 l01 = sum2_rm(m01, vv), l23 = sum2_rm(m23, vv);
+          const float lo[4] = {l01.x, l01.y, l23.x, l23.y};
+          unsigned pass = 0u;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) pass |= (lo[q] < vhi[c][q] ? 1u : 0u) << q;
+          if (__any_sync(kFullMask, pass != 0u)) {
+            const double vk = __shfl_sync(kFullMask, v[c][2 * h + par], kk);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (!((pass >> q) & 1u)) continue;
+              const int pos = 2 * lane + (q & 1) + 64 * (q >> 1);
+              const double cand = __dadd_rn(__ldg(diag + pos * dpos + k * dk), vk);
+              if (cand < v[c][q]) {
+                v[c][q] = cand;
+                vlo[c][q] = f64_down(cand);
+                vhi[c][q] = f64_up(cand);
+                pk[c] = __byte_perm(pk[c], (unsigned)k, 0x3210 ^ ((0x3210 & (0xF << (4 * q))) ^ (4 << (4 * q))));
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  // D and P where the line improved; the phase-4 operand pack everywhere.
+  Pack *dst = is_row ? &packB[other] : &packA[other];
+  bool ex = true;
+#pragma unroll
+  for (int c = 0; c < LINES; ++c) {
+    const int line = line0 + c;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const unsigned kq = (pk[c] >> (8 * q)) & 0xFFu;
+      if (kq != 0xFFu) {  // improved: inside the matrix
+        const int pos = 2 * lane + (q & 1) + 64 * (q >> 1);
+        const int64_t g = g0 + line * sl + pos * sp;
+        D[g] = v[c][q];
+        if (P) P[g] = base_r + (int)kq;
+      }
+      ex = ex && vlo[c][q] == vhi[c][q];
+    }
+#pragma unroll
+    for (int hq = 0; hq < 2; ++hq) {  // positions 2 lane + 64 hq + {0, 1}: k-pair lane + 32 hq
+      const int kp = lane + 32 * hq, pos = 2 * kp;
+      dst->lo[line >> 6][kp][line & 63] = packf2(vlo[c][2 * hq], vlo[c][2 * hq + 1]);
+      dst->hi[line >> 6][kp][line & 63] = packf2(vhi[c][2 * hq], vhi[c][2 * hq + 1]);
+      *reinterpret_cast<float2 *>(&dst->rlo[line][pos]) = make_float2(vlo[c][2 * hq], vlo[c][2 * hq + 1]);
+      *reinterpret_cast<float2 *>(&dst->rhi[line][pos]) = make_float2(vhi[c][2 * hq], vhi[c][2 * hq + 1]);
+      *reinterpret_cast<double2 *>(&dst->r64[line][pos]) = make_double2(v[c][2 * hq], v[c][2 * hq + 1]);
+    }
+  }
+  if (__syncthreads_or(!ex) && tid == 0) dst->exact = 0;
 }
 
 // ---------------------------------------------------------------- products
-// A CTA computes one 128 x 64 half of an output block (two CTAs per block,
-// three CTAs per SM):
-// MODE 0: phase 4, C = (I,J), A = packA[I], B = packB[J] (grid: per block set)
-// MODE 1: phase 2, C = (r,J), A = diagA,    B = packB[J] (grid 2 (R-1)), re-packs C into packB[J]
-// MODE 2: phase 3, C = (I,r), A = packA[I], B = diagB    (grid 2 (R-1)), re-packs C into packA[I]
+// Phase 4: a CTA computes one 128 x 64 half of an output block C = (I,J)
+// (two CTAs per block, three CTAs per SM) from A = packA[I] and B = packB[J],
+// both final for the round.
 //
 // Only the lower bounds enter the main loop.  X = min_k lo_k is a lower bound
 // of the exact FP64 minimum s* (lo_k <= s_k for every k), so X >= ru(old)
@@ -327,7 +423,7 @@ __device__ __forceinline__ void issue_slab(ProdSmem &sm, int st, const Pack *A, 
   bulk_g2s(&sm.Blo[st][0][0], &B->lo[hJ][s * KP][0], SLAB_BYTES, &sm.bar[st]);
 }
 
-// Block sets of one phase-4 launch (MODE 0; grid: 2 CTAs per block).
+// Block sets of one phase-4 launch (grid: 2 CTAs per block).
 constexpr int kSetAll = 0;   // all (R-1)^2 blocks off row/column r
 constexpr int kSetNext = 1;  // the 2R-3 blocks in row r+1 or column r+1
 constexpr int kSetRest = 2;  // the (R-2)^2 blocks off rows/columns r and r+1
@@ -343,57 +439,48 @@ __device__ __forceinline__ double f32_as_f64(float x) { return __longlong_as_dou
 // less than scanning every candidate again to find the k that reaches X.
 constexpr int kEagerRounds64 = APSP_F64_EAGER_ROUNDS;
 
-template <int MODE, bool EAGER = false>
+template <bool EAGER>
 __global__ void __launch_bounds__(THREADS, EAGER ? 2 : 3)
     fw64_product(double *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n, int r, int R,
-                 Pack *packA, Pack *packB, const Pack *diagA, const Pack *diagB, int set) {
+                 const Pack *packA, const Pack *packB, int set) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   ProdSmem &sm = *reinterpret_cast<ProdSmem *>(smem_raw);
   const int tile = blockIdx.x >> 1, hJ = blockIdx.x & 1;
   int I, J;
-  if (MODE == 0) {
-    if (set == kSetAll) {
-      I = tile / (R - 1);
-      J = tile % (R - 1);
-      I += (I >= r);
-      J += (J >= r);
-    } else if (set == kSetNext) {  // row r+1, then column r+1: the next round's K1/K2 input
-      if (tile < R - 1) {
-        I = r + 1;
-        J = tile + (tile >= r);
-      } else {
-        I = tile - (R - 1);
-        I += (I >= r);
-        I += (I >= r + 1);
-        J = r + 1;
-      }
-    } else {  // the rest: rows and columns other than r and r+1
-      I = tile / (R - 2);
-      J = tile % (R - 2);
+  if (set == kSetAll) {
+    I = tile / (R - 1);
+    J = tile % (R - 1);
+    I += (I >= r);
+    J += (J >= r);
+  } else if (set == kSetNext) {  // row r+1, then column r+1: the next round's K1/K2 input
+    if (tile < R - 1) {
+      I = r + 1;
+      J = tile + (tile >= r);
+    } else {
+      I = tile - (R - 1);
       I += (I >= r);
       I += (I >= r + 1);
-      J += (J >= r);
-      J += (J >= r + 1);
+      J = r + 1;
     }
-  } else if (MODE == 1) {
-    I = r;
-    J = tile + (tile >= r);
-  } else {
-    I = tile + (tile >= r);
-    J = r;
+  } else {  // the rest: rows and columns other than r and r+1
+    I = tile / (R - 2);
+    J = tile % (R - 2);
+    I += (I >= r);
+    I += (I >= r + 1);
+    J += (J >= r);
+    J += (J >= r + 1);
   }
-  const Pack *A = MODE == 1 ? diagA : &packA[I];
-  const Pack *B = MODE == 2 ? diagB : &packB[J];
+  const Pack *A = &packA[I];
+  const Pack *B = &packB[J];
   const int baseI = I * T, baseJ = J * T + hJ * H, baseK = r * T;
   const int mI = min(T, n - baseI), mJ = min(H, n - baseJ), mK = min(T, n - baseK);
-  if (mJ <= 0) return;  // an empty half: its packs already hold +inf (uniform exit, no barrier used)
+  if (mJ <= 0) return;  // an empty half of the last (narrow) block (uniform exit, no barrier used)
   const int nslab = (mK + KS - 1) / KS;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int ty = 4 * w + (lane >> 3), tx = lane & 7;
   const float FINF = __int_as_float(0x7f800000);
   // Both operands hold floats only: a candidate's upper bound is ru of the
-  // same operands as its lower bound (read once here: phases 2/3 may clear
-  // the flag of the pack they re-pack while a sibling CTA still reads it).
+  // same operands as its lower bound.
   const bool exact = A->exact && B->exact;
 
   if (tid == 0) {
@@ -417,7 +504,7 @@ __global__ void __launch_bounds__(THREADS, EAGER ? 2 : 3)
     const bool ok = mbar_wait(&sm.bar[st], (s / STAGES) & 1);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
-        atomicExch(&g_device_error, APSP_ECUDA);
+        report_wait_timeout();
         for (int s2 = s + 1; s2 < nslab && s2 < s + STAGES; ++s2)
           mbar_wait(&sm.bar[s2 % STAGES], (s2 / STAGES) & 1);
       }
@@ -732,65 +819,9 @@ __global__ void __launch_bounds__(THREADS, EAGER ? 2 : 3)
       }
     }
   }
-  if (MODE == 0) return;
-  // Phases 2/3: re-pack this half of the updated block for the round's phase 4.
-  __syncthreads();
-  Pack *dst = MODE == 1 ? &packB[J] : &packA[I];
-  bool ex = true;  // every value this CTA re-packs is a float
-#pragma unroll
-  for (int rr = 0; rr < 4; rr += 2) {
-    const int i0p = row4(rr, ty);  // rows i0p, i0p + 1 of the block
-#pragma unroll
-    for (int cc = 0; cc < 8; cc += 2) {
-      const int j0l = col8(cc, tx);  // columns j0l, j0l + 1 of the half
-      const int jb = jb0 + j0l;      // ... of the block
-      double v[2][2];
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-          v[a][c] = (i0p + a < mI && j0l + c < mJ)
-                        ? D[(int64_t)(baseI + i0p + a) * ld + baseJ + j0l + c]
-                        : inf<double>();
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int i = i0p + a, j = jb + c;
-          const float vl = f64_down(v[a][c]), vh = f64_up(v[a][c]);
-          ex = ex && vl == vh;
-          if (MODE == 1) {  // B operand: [j][k = i]
-            dst->rlo[j][i] = vl;
-            dst->rhi[j][i] = vh;
-            dst->r64[j][i] = v[a][c];
-          } else {  // A operand: [i][k = j]
-            dst->rlo[i][j] = vl;
-            dst->rhi[i][j] = vh;
-            dst->r64[i][j] = v[a][c];
-          }
-        }
-      if (MODE == 1) {  // pairs along k = rows i0p, i0p + 1; column jb + c of the B pack
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          dst->lo[(jb + c) >> 6][i0p / 2][(jb + c) & 63] = packf2(f64_down(v[0][c]), f64_down(v[1][c]));
-          dst->hi[(jb + c) >> 6][i0p / 2][(jb + c) & 63] = packf2(f64_up(v[0][c]), f64_up(v[1][c]));
-        }
-      } else {  // pairs along k = block columns jb, jb + 1; row i of the A pack
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const int i = i0p + a;
-          dst->lo[i >> 6][jb / 2][i & 63] = packf2(f64_down(v[a][0]), f64_down(v[a][1]));
-          dst->hi[i >> 6][jb / 2][i & 63] = packf2(f64_up(v[a][0]), f64_up(v[a][1]));
-        }
-      }
-    }
-  }
-  // The flag stays 1 only if the values before (packing) and after (both
-  // halves) are all floats; a half with an inexact value clears it.
-  if (__syncthreads_or(!ex) && tid == 0) dst->exact = 0;
 }
 
-static int g_smem_k1[64], g_smem_k2a[64], g_smem_p0[64], g_smem_p0e[64], g_smem_p1[64], g_smem_p2[64];
+static int g_smem_k1[64], g_smem_k2[64], g_smem_p0[64], g_smem_p0e[64];
 
 }  // namespace f64
 
@@ -799,41 +830,37 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
   using namespace f64;
   const int R = (n + T - 1) / T;
   int st;
-  const int smem1 = (int)sizeof(K1Smem), smem2a = T * (T + 1) * 8, smemp = (int)sizeof(ProdSmem);
+  const int smem1 = (int)sizeof(K1Smem), smemp = (int)sizeof(ProdSmem);
   if ((st = ensure_smem(fw64_diag, smem1, g_smem_k1))) return st;
-  if ((st = ensure_smem(fw64_pack_panels, smem2a, g_smem_k2a))) return st;
-  if ((st = ensure_smem(fw64_product<0>, smemp, g_smem_p0))) return st;
-  if ((st = ensure_smem(fw64_product<0, true>, smemp, g_smem_p0e))) return st;
-  if ((st = ensure_smem(fw64_product<1>, smemp, g_smem_p1))) return st;
-  if ((st = ensure_smem(fw64_product<2>, smemp, g_smem_p2))) return st;
+  if ((st = ensure_smem(fw64_lines, k2::SMEM, g_smem_k2))) return st;
+  if ((st = ensure_smem(fw64_product<false>, smemp, g_smem_p0))) return st;
+  if ((st = ensure_smem(fw64_product<true>, smemp, g_smem_p0e))) return st;
   // Operand packs: two sets by round parity (so that phases 1-3 of round
   // r+1 can pack while phase 4 of round r still reads), each R column-panel
-  // packs, R row-panel packs and the diagonal block as A and as B operand.
+  // packs (A operands) and R row-panel packs (B operands).
   struct PackSet {
-    Pack *A, *B, *dA, *dB;
+    Pack *A, *B;
   } ps[2]{};
   char *scratch = nullptr;
   if (R > 1) {
-    if (cudaMallocAsync((void **)&scratch, sizeof(Pack) * 2 * (2 * (size_t)R + 2), s) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&scratch, sizeof(Pack) * 2 * (2 * (size_t)R), s) != cudaSuccess) {
       cudaGetLastError();
       return APSP_ENOMEM;
     }
     for (int q = 0; q < 2; ++q) {
-      Pack *base = reinterpret_cast<Pack *>(scratch) + (size_t)q * (2 * R + 2);
-      ps[q] = {base, base + R, base + 2 * R, base + 2 * R + 1};
+      Pack *base = reinterpret_cast<Pack *>(scratch) + (size_t)q * (2 * R);
+      ps[q] = {base, base + R};
     }
   }
   auto diag_and_panels = [&](int r, cudaStream_t stm) {
     const PackSet &p = ps[r & 1];
     {
       PhaseScope sc(1, stm);
-      fw64_diag<<<1, K1_THREADS, smem1, stm>>>(D, ld, P, n, r, p.dA, p.dB);
+      fw64_diag<<<1, K1_THREADS, smem1, stm>>>(D, ld, P, n, r, R, p.A, p.B);
     }
     if (R > 1) {
       PhaseScope sc(2, stm);
-      fw64_pack_panels<<<2 * (R - 1), K2A_THREADS, smem2a, stm>>>(D, ld, n, r, R, p.A, p.B);
-      fw64_product<1><<<2 * (R - 1), THREADS, smemp, stm>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, 0);
-      fw64_product<2><<<2 * (R - 1), THREADS, smemp, stm>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, 0);
+      fw64_lines<<<2 * (R - 1) * k2::PARTS, k2::K2_THREADS, k2::SMEM, stm>>>(D, ld, P, n, r, R, p.A, p.B);
     }
   };
   auto phase4 = [&](int r, int set, int blocks) {
@@ -841,9 +868,9 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
     const PackSet &p = ps[r & 1];
     PhaseScope sc(3, s);
     if (r < kEagerRounds64)
-      fw64_product<0, true><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, set);
+      fw64_product<true><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, set);
     else
-      fw64_product<0><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, p.dA, p.dB, set);
+      fw64_product<false><<<2 * blocks, THREADS, smemp, s>>>(D, ld, P, n, r, R, p.A, p.B, set);
   };
   // Look-ahead as in the FP32 path: phase 4 of round r updates row and
   // column r+1 first; phases 1-3 of round r+1 then run on a second stream of
@@ -900,12 +927,6 @@ int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s
   return status_from(e);
 }
 
-int take_device_error_f64() {
-  int v = 0;
-  const int zero = 0;
-  if (cudaMemcpyFromSymbol(&v, g_device_error, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
-  if (v != 0 && cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
-  return v;
-}
+int take_device_error_f64() { return take_tu_device_error(); }
 
 }  // namespace apsp

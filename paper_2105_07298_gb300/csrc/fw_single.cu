@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(mp32::THREADS, EAGER ? APSP_K3_EAGER_MIN_BLOCK
       // A copy never completed: record it, wait (bounded) for the other
       // copies this CTA issued, and leave without touching D or P.
       if (tid == 0) {
-        atomicExch(&g_device_error, APSP_ECUDA);
+        report_wait_timeout();
         for (int s2 = s + 1; s2 < nslab && s2 < s + STAGES; ++s2)
           mbar_wait(&sm.bar[s2 % STAGES], (s2 / STAGES) & 1);
       }
@@ -723,6 +723,7 @@ static int g_smem_k1f[64], g_smem_p2f[64], g_smem_k3[64], g_smem_k3e[64];
 
 int run_fw_f64_interval(double *D, int n, int64_t ld, int32_t *P, cudaStream_t s);
 int take_device_error_f64();
+int take_device_error_checks();
 
 static void path_init(int32_t *P, int64_t n, int64_t ld, cudaStream_t s) {
   const int64_t total = n * n;
@@ -879,6 +880,8 @@ APSP_EXPORT const char *apsp_status_string(int status) {
     case APSP_ENOMEM: return "APSP_ENOMEM: device allocation failed";
     case APSP_EUNSUPPORTED: return "APSP_EUNSUPPORTED: outside supported sizes";
     case APSP_ETOODEEP: return "APSP_ETOODEEP: path recursion deeper than the walk stack";
+    case APSP_ENEGCYCLE: return "APSP_ENEGCYCLE: negative cycle (a diagonal distance is below 0)";
+    case APSP_ETIMEOUT: return "APSP_ETIMEOUT: a kernel's bounded wait for an asynchronous copy ran out";
     default: return "APSP: unknown status";
   }
 }
@@ -935,11 +938,8 @@ APSP_EXPORT int apsp_profile_records(int32_t *phase, float *ms, int64_t cap, int
 
 APSP_EXPORT int apsp_device_status(void *stream) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return APSP_ECUDA;
-  int v = 0;
-  const int zero = 0;
-  if (cudaMemcpyFromSymbol(&v, apsp::g_device_error, sizeof(int)) != cudaSuccess) return APSP_ECUDA;
-  if (v != 0 && cudaMemcpyToSymbol(apsp::g_device_error, &zero, sizeof(int)) != cudaSuccess)
-    return APSP_ECUDA;
+  const int v = apsp::take_tu_device_error();
   const int v64 = apsp::take_device_error_f64();
-  return v != 0 ? v : v64;
+  const int vc = apsp::take_device_error_checks();
+  return v != 0 ? v : v64 != 0 ? v64 : vc;
 }

@@ -60,3 +60,17 @@ def test_argument_errors_without_gpu():
     off = (ctypes.c_int64 * 1)(0)
     assert L.apsp_batched_plan_create(n, off, 1, ctypes.byref(plan)) == 4
     assert L.apsp_batched_plan_create(None, None, 1, ctypes.byref(plan)) == 1
+
+
+def test_new_entry_points_reject_bad_arguments_without_gpu():
+    """Argument checks of the status, self-test and packed-backward entry points
+    return before any CUDA call."""
+    L = apsp.load()
+    assert L.apsp_check_negative_cycle(None, 3, 4, 4, None) == apsp.APSP_EINVAL
+    assert L.apsp_check_negative_cycle(None, 4, -1, 4, None) == apsp.APSP_EINVAL
+    assert L.apsp_wait_timeout_selftest(0, None) == apsp.APSP_EINVAL
+    assert L.apsp_wait_timeout_selftest((1 << 22) + 1, None) == apsp.APSP_EINVAL
+    assert L.apsp_fw_backward_packed_f32(None, None, None, None, None, None, -1, None, None) == apsp.APSP_EINVAL
+    for st in range(8):
+        assert L.apsp_status_string(st).startswith(b"APSP_")
+    assert L.apsp_status_string(7) == b"APSP_ETIMEOUT: a kernel's bounded wait for an asynchronous copy ran out"

@@ -61,3 +61,25 @@ def test_phase4_work_per_round_counts_every_k_of_the_round():
     assert bench.phase3_relax_per_round(1024, 128) == pytest.approx((1024 - 128) ** 2 * 128)
     # a single block has no phase 4
     assert bench.phase3_relax_per_round(100, 128) == 0
+
+
+def test_recorded_profiler_captures_stay_small():
+    """Every ncu command recorded under profiles/ that collects more than the
+    per-launch duration captures at most three launches (-c), and every one
+    names --clock-control none: the full-size workload is only ever listed
+    with durations (one pass)."""
+    import glob
+    import re
+    cmds = []
+    for path in glob.glob(os.path.join(bench.ROOT, "profiles", "*")):
+        txt = open(path).read().replace("\\\n", " ")
+        for m in re.finditer(r"^[#\s]*(ncu\s(?!-i\b).*)$", txt, flags=re.M):
+            cmds.append((os.path.basename(path), m.group(1)))
+    assert cmds
+    for name, cmd in cmds:
+        assert "--clock-control none" in cmd, (name, cmd)
+        metrics = re.search(r"--metrics\s+(\S+)", cmd)
+        only_duration = metrics is not None and metrics.group(1) == "gpu__time_duration.sum" and "--set" not in cmd
+        if not only_duration:
+            count = re.search(r"\s-c\s+(\d+)", cmd)
+            assert count and int(count.group(1)) <= 3, (name, cmd)

@@ -93,3 +93,72 @@ def test_backward_errors_and_empty():
     lib = apsp.load()
     assert lib.apsp_fw_backward_f32(None, None, None, None, 0, 0, 1, 0, None, None) == apsp.APSP_OK
     assert lib.apsp_fw_backward_f32(None, None, None, None, 4, 4, 1, 16, None, None) == apsp.APSP_EINVAL
+
+
+def test_packed_uneven_backward_matches_oracle():
+    """Packed batch of uneven graphs (odd sizes, 16-byte aligned offsets):
+    forward through one batched launch, backward through the packed scatter
+    kernel, each graph against the oracle gradient; gaps get zero gradient."""
+    from paper_2105_07298_gb300 import batched as B
+    sizes = [33, 5, 130, 64, 1, 97, 256]
+    off = B.packed_offsets(sizes)
+    total = B.packed_numel(sizes)
+    Wp = np.zeros(total, dtype=np.float32)
+    gDp = np.zeros(total, dtype=np.float32)
+    mats = []
+    for g, (n, o) in enumerate(zip(sizes, off)):
+        W = graphgen.dense_graph(n, 0.4, 40 + g, weights="real", lo=0.5, hi=2.0)
+        mats.append(W)
+        Wp[o:o + n * n] = W.reshape(-1)
+        gDp[o:o + n * n] = graphgen.normal((n, n), 60 + g).reshape(-1)
+    Wt = torch.from_numpy(Wp).to(DEV).requires_grad_(True)
+    D = apsp.shortest_path_distances_packed(Wt, sizes, off)
+    gD = torch.from_numpy(gDp).to(DEV)
+    (D.masked_fill(torch.isinf(D), 0) * gD).sum().backward()
+    gW = Wt.grad.cpu().numpy()
+    Dh = D.detach().cpu().numpy()
+    inside = np.zeros(total, dtype=bool)
+    for g, (n, o) in enumerate(zip(sizes, off)):
+        inside[o:o + n * n] = True
+        D64, P64 = oracle.fw(mats[g].astype(np.float64))
+        fin = np.isfinite(D64)
+        np.testing.assert_allclose(Dh[o:o + n * n].reshape(n, n)[fin], D64[fin], rtol=1e-5)
+        gd = gDp[o:o + n * n].reshape(n, n).astype(np.float64)
+        ref = oracle.fw_backward(gd, P64, D64)
+        bound = _grad_tol(gd, P64, D64)
+        got = gW[o:o + n * n].reshape(n, n)
+        assert (np.abs(got - ref) <= 1e-5 * np.maximum(bound, 1e-30) + 1e-30).all(), g
+    assert (gW[~inside] == 0).all()
+    lib = apsp.load()
+    assert lib.apsp_fw_backward_packed_f32(None, None, None, None, None, None, 0, None, None) == apsp.APSP_OK
+    assert lib.apsp_fw_backward_packed_f32(None, None, None, None, None, None, 3, None, None) == apsp.APSP_EINVAL
+
+
+@pytest.mark.parametrize("Bn,n", [(3, 33), (2, 1030)])
+def test_autograd_stack_odd_and_large_n(Bn, n):
+    """(B, n, n) stacks whose graphs are not 16-byte aligned back to back (odd n)
+    or too large for the batched kernel (n > 1024) still solve and differentiate.
+    The reference gradient walks the forward's own path matrix (from a second,
+    identical solve), which must itself be valid; D is held to the FP64 oracle."""
+    from paper_2105_07298_gb300 import backward as bw
+    Ws = np.stack([graphgen.dense_graph(n, 0.4, 900 + b, weights="real", lo=0.5, hi=2.0) for b in range(Bn)])
+    gD = graphgen.normal((Bn, n, n), 13)
+    Wt = torch.from_numpy(Ws).to(DEV).requires_grad_(True)
+    D = apsp.shortest_path_distances(Wt)
+    D.backward(torch.from_numpy(gD).to(DEV))
+    gW = Wt.grad.cpu().numpy()
+    Dh = D.detach().cpu().numpy()
+    D2 = torch.from_numpy(Ws).to(DEV).contiguous()
+    P2 = torch.empty(D2.shape, dtype=torch.int32, device=DEV)
+    bw._solve_stack(D2, P2)
+    np.testing.assert_array_equal(D2.cpu().numpy(), Dh)
+    Ph = P2.cpu().numpy()
+    for b in range(Bn):
+        D64 = oracle.fw(Ws[b].astype(np.float64))[0]
+        fin = np.isfinite(D64)
+        np.testing.assert_allclose(Dh[b][fin], D64[fin], rtol=1e-5)
+        pairs = list(zip(*np.random.default_rng(b).integers(0, n, (2, 2000))))
+        assert oracle.check_paths(Ws[b], Dh[b], Ph[b], pairs=pairs, rtol=1e-5) == 0
+        ref = oracle.fw_backward(gD[b], Ph[b], Dh[b])
+        bound = _grad_tol(gD[b], Ph[b], Dh[b])
+        assert (np.abs(gW[b] - ref) <= 1e-5 * np.maximum(bound, 1e-30) + 1e-30).all()

@@ -139,3 +139,42 @@ def test_autotuner_picks_a_variant_per_class():
     assert set(res) == set(range(B.num_classes()))
     for c, r in res.items():
         assert r["variant"] == int(np.argmin(r["ms"])) and B.get_variant(c) == r["variant"]
+
+
+def test_plan_captured_in_cuda_graph_replays_on_fresh_inputs():
+    """BatchedPlan.run captured into a CUDA graph (one memset + one persistent
+    launch), then replayed twice on fresh inputs copied into the captured
+    buffers: every sampled graph matches the oracle and its paths are valid."""
+    rng = np.random.default_rng(11)
+    sizes = rng.integers(16, 513, 96).astype(np.int64)
+    sizes[:3] = (16, 512, 257)
+    off = B.packed_offsets(sizes)
+    total = B.packed_numel(sizes)
+    D = torch.empty(total, dtype=torch.float32, device=DEV)
+    P = torch.empty(total, dtype=torch.int32, device=DEV)
+    plan = B.BatchedPlan(sizes, off)
+    W0 = graphgen.batched_graphs_torch(sizes, 0.3, 21, off, total, device=DEV)
+    D.copy_(W0)
+    plan.run(D, P)  # warm-up outside capture (module load, shared-memory limit)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run(D, P)
+    torch.cuda.current_stream().wait_stream(s)
+    for seed in (31, 32):  # two replays, each on a new batch of graphs
+        W = graphgen.batched_graphs_torch(sizes, 0.3, seed, off, total, device=DEV)
+        D.copy_(W)
+        P.fill_(-7)
+        g.replay()
+        torch.cuda.synchronize()
+        Wh, Dh, Ph = W.cpu().numpy(), D.cpu().numpy(), P.cpu().numpy()
+        for gi in list(rng.choice(len(sizes), 10, replace=False)) + [0, 1, 2]:
+            n, o = int(sizes[gi]), int(off[gi])
+            Wg = Wh[o:o + n * n].reshape(n, n)
+            Dg, Pg = Dh[o:o + n * n].reshape(n, n), Ph[o:o + n * n].reshape(n, n)
+            np.testing.assert_array_equal(Dg, oracle.fw(Wg)[0])
+            assert oracle.check_paths(Wg, Dg, Pg) == 0
+    plan.close()

@@ -70,11 +70,15 @@ def test_real_weights_f32_match_blocked_oracle_bitwise(n):
 
 
 @pytest.mark.parametrize("n,p", [(70, 0.4), (200, 0.4), (333, 0.4), (300, 0.05), (513, 0.4)])
-def test_real_weights_f64_within_1e12(n, p):
-    """FP64 (phases 2/3 through the closed diagonal block): within 1e-12 relative
-    of the exact FP64 distances; phase 1 and 4 candidate sums are IEEE FP64."""
+def test_real_weights_f64_match_blocked_oracle_bitwise(n, p):
+    """FP64 follows the paper's four phases in its k order with IEEE FP64 sums:
+    D and P bit-exact with the oracle's blocked FW at the library's block size,
+    and within 1e-12 relative of the classic FP64 FW."""
     W = graphgen.dense_graph(n, p, 177 + n, weights="real", lo=0.5, hi=2.0, dtype=np.float64)
     D, P, _ = _run(W, np.float64)
+    Db, Pb = oracle.bfw(W, apsp.block_size(torch.float64))
+    np.testing.assert_array_equal(D, Db)
+    np.testing.assert_array_equal(P, Pb)
     D64, _ = oracle.fw(W)
     fin = np.isfinite(D64)
     np.testing.assert_array_equal(np.isfinite(D), fin)
@@ -86,7 +90,8 @@ def test_real_weights_f64_within_1e12(n, p):
 
 def test_f64_values_beyond_float_range_and_fractions():
     """FP64 inputs FP32 cannot hold exactly (2^-30 fractions, magnitudes near 1e300,
-    tiny values): the interval filter must still give exact FP64 results."""
+    tiny values): the interval filter must still give exact FP64 results, bit
+    for bit those of the sequential blocked FW."""
     rng = np.random.default_rng(8)
     n = 260
     W = graphgen.dense_graph(n, 0.3, 99, dtype=np.float64)
@@ -102,6 +107,9 @@ def test_f64_values_beyond_float_range_and_fractions():
         ok = np.isfinite(Dref)
         np.testing.assert_array_equal(np.isfinite(D), ok)
         np.testing.assert_allclose(D[ok], Dref[ok], rtol=1e-12)
+        Db, Pb = oracle.bfw(Ws, apsp.block_size(torch.float64))
+        np.testing.assert_array_equal(D, Db)
+        np.testing.assert_array_equal(P, Pb)
 
 
 def test_config_small_n1024_full():
@@ -193,13 +201,14 @@ def _dijkstra_check(D_dev, W_host, srcs):
                                      (65536, torch.float32)])
 def test_full_size_sampled_rows(n, dtype):
     """Full-size blocked FW (edge probability 0.5, integer weights): sampled
-    rows against Dijkstra (exact) and sampled paths against the weights."""
+    rows against Dijkstra (exact; 64 rows at n = 16384, 8 at the larger sizes)
+    and 40 sampled paths per row against the weights."""
     W = graphgen.dense_graph_torch(n, 0.5, 20210517, dtype=dtype, device=DEV)
     W_host = W.cpu().numpy()
     P = torch.empty((n, n), dtype=torch.int32, device=DEV)
     apsp.apsp_fw(W, P)
     torch.cuda.synchronize()
-    srcs = np.random.default_rng(n).integers(0, n, 8)
+    srcs = np.random.default_rng(n).integers(0, n, 64 if n == 16384 else 8)
     _dijkstra_check(W, W_host, srcs)
     # path validation on sampled pairs, reading rows of P and D on demand
     rows = sorted(set(srcs.tolist()))
@@ -279,3 +288,39 @@ def test_solve_captured_in_cuda_graph(dtype):
     torch.cuda.synchronize()
     assert torch.equal(D, D0) and torch.equal(P, P0)
     assert apsp.device_status() == apsp.APSP_OK
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_negative_cycle_check(dtype):
+    """A graph with a negative cycle leaves D[i][i] < 0 on the cycle's vertices;
+    the check reports it, and reports nothing for the same graph without it."""
+    n = 300
+    W = graphgen.dense_graph(n, 0.3, 31, dtype=dtype)
+    D, _, _ = _run(W, dtype)
+    Dt = torch.from_numpy(D).to(DEV)
+    assert not apsp.check_negative_cycle(Dt)
+    Wn = W.copy()
+    Wn[5, 250] = -1000.0  # cycle 5 -> 250 -> ... -> 5 of weight below zero
+    D, _, _ = _run(Wn, dtype)
+    assert (np.diag(D)[[5, 250]] < 0).all()
+    assert apsp.check_negative_cycle(torch.from_numpy(D).to(DEV))
+    lib = apsp.load()
+    assert lib.apsp_check_negative_cycle(None, 4, 0, 0, None) == apsp.APSP_OK
+    assert lib.apsp_check_negative_cycle(None, 4, 3, 3, None) == apsp.APSP_EINVAL
+    assert lib.apsp_check_negative_cycle(Dt.data_ptr(), 2, n, n, None) == apsp.APSP_EINVAL
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """The bounded mbarrier wait of the bulk-copy kernels, on a barrier nothing
+    completes, gives up, records APSP_ETIMEOUT and returns: the status reads
+    back once (then clears), and the next solve is correct."""
+    assert apsp.device_status() == apsp.APSP_OK
+    apsp.wait_timeout_selftest(4096)
+    assert apsp.device_status() == apsp.APSP_ETIMEOUT
+    assert apsp.device_status() == apsp.APSP_OK
+    W = graphgen.dense_graph(260, 0.3, 8)
+    D, P, _ = _run(W, np.float32)
+    np.testing.assert_array_equal(D, oracle.fw(W)[0])
+    assert apsp.device_status() == apsp.APSP_OK
+    with pytest.raises(apsp.ApspError):
+        apsp.wait_timeout_selftest(0)

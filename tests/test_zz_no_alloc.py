@@ -3,10 +3,13 @@
 It serves callers that cannot allocate device memory at call time (a serving
 loop that forbids cudaMalloc on its hot path, memory owned by a foreign
 allocator, embeddings where hidden allocations are errors): its work list
-lives in a fixed device array of the library.  Checked against the allocating
-entry point on two calls in a row (the shared array keeps the previous call's
-contents, which must not leak into the next result).  This file is collected
-last on purpose, and must pass alone in a fresh process as well.
+lives in a fixed device array of the library.  Checked graph by graph against
+the CPU oracle and against the allocating entry point, on two calls in a row
+(the shared array keeps the previous call's contents, which must not leak into
+the next result), and checked to allocate nothing: neither the default
+stream-ordered memory pool, nor torch's caching allocator, nor the device's
+free memory move across a call.  This file is collected last on purpose, and
+must pass alone in a fresh process as well.
 """
 import ctypes
 
@@ -15,11 +18,40 @@ import pytest
 import torch
 
 import graphgen
+import oracle
 import paper_2105_07298_gb300 as apsp
 from paper_2105_07298_gb300 import batched as B
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
+
+# CUmemPool_attribute values of the driver API (cuda.h)
+_USED_MEM_CURRENT, _USED_MEM_HIGH, _RESERVED_MEM_CURRENT = 7, 8, 5
+
+
+class _DriverMemory:
+    """Device memory counters read through the CUDA driver API (libcuda)."""
+
+    def __init__(self):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        self.pool = ctypes.c_void_p()
+        dev = ctypes.c_int()
+        assert self.cu.cuCtxGetDevice(ctypes.byref(dev)) == 0
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def pool_attr(self, attr):
+        v = ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high_watermark(self):
+        zero = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, _USED_MEM_HIGH, ctypes.byref(zero)) == 0
+
+    def free_bytes(self):
+        free, total = ctypes.c_size_t(), ctypes.c_size_t()
+        assert self.cu.cuMemGetInfo_v2(ctypes.byref(free), ctypes.byref(total)) == 0
+        return free.value
 
 
 def _packed(sizes, seed):
@@ -29,33 +61,44 @@ def _packed(sizes, seed):
     return W, off
 
 
-def _call(fn, W, sizes, off):
+def _call(fn, D, P, sizes, off):
     lib = apsp.load()
     n = np.ascontiguousarray(sizes, dtype=np.int32)
     o = np.ascontiguousarray(off, dtype=np.int64)
-    D = W.clone()
-    P = torch.full_like(D, 7, dtype=torch.int32)
     st = getattr(lib, fn)(ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(P.data_ptr()),
                           n.ctypes.data_as(ctypes.c_void_p), o.ctypes.data_as(ctypes.c_void_p),
                           len(n), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     torch.cuda.synchronize()
-    return st, D, P
+    return st
 
 
-def test_no_alloc_matches_allocating_entry_point_twice():
+def test_no_alloc_matches_oracle_and_allocating_entry_point_twice():
     runs = [([300, 17, 64, 129, 1, 512, 250, 96], 3), ([40, 256, 257, 3, 128, 65], 4)]
-    for sizes, seed in runs:  # two calls in a row, different batches
+    mem = _DriverMemory()
+    for call, (sizes, seed) in enumerate(runs):  # two calls in a row, different batches
         W, off = _packed(sizes, seed)
-        st_ref, D_ref, P_ref = _call("apsp_fw_batched_f32", W, sizes, off)
-        st, D, P = _call("apsp_fw_batched_f32_noalloc", W, sizes, off)
-        assert st_ref == apsp.APSP_OK and st == apsp.APSP_OK
-        # integer weights: every sum is exact, so the distances agree bit for bit;
-        # compare graph by graph (the alignment gaps between graphs hold NaN and
-        # must stay untouched)
+        D_ref, P_ref = W.clone(), torch.full_like(W, 7, dtype=torch.int32)
+        assert _call("apsp_fw_batched_f32", D_ref, P_ref, sizes, off) == apsp.APSP_OK
+        D, P = W.clone(), torch.full_like(W, 7, dtype=torch.int32)
+        torch.cuda.synchronize()
+        free0 = mem.free_bytes()
+        mem.reset_high_watermark()
+        torch_allocs0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+        assert _call("apsp_fw_batched_f32_noalloc", D, P, sizes, off) == apsp.APSP_OK
+        if call > 0:  # the first call on the device may load the library's module
+            assert mem.pool_attr(_USED_MEM_HIGH) == 0
+            assert mem.free_bytes() == free0
+        assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == torch_allocs0
+        Wh, Dh, Ph = W.cpu().numpy(), D.cpu().numpy(), P.cpu().numpy()
         for n, o in zip(sizes, off):
             sl = slice(int(o), int(o) + n * n)
+            # integer weights: every sum is exact, so the distances agree bit for bit
+            Wg = Wh[sl].reshape(n, n)
+            np.testing.assert_array_equal(Dh[sl].reshape(n, n), oracle.fw(Wg)[0])
+            assert oracle.check_paths(Wg, Dh[sl].reshape(n, n), Ph[sl].reshape(n, n)) == 0
             assert torch.equal(D[sl], D_ref[sl])
             assert torch.equal(P[sl], P_ref[sl])
+        # the alignment gaps between graphs hold NaN and must stay untouched
         gaps = torch.isnan(W)
         assert torch.isnan(D[gaps]).all() and torch.isnan(D_ref[gaps]).all()
 
