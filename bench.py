@@ -22,7 +22,9 @@ The same JSON line also carries:
 ``--impl reference``: the CPU oracle timed on the host cores, each step a
 bounded sample (a prefix of the outer k loop) of the same workload.
 Multi-GPU (torchrun): every rank solves its own graph (independent problems,
-weak scaling, no data-path collective); timing is the max over ranks.
+weak scaling, no data-path collective); timing is the max over ranks.  The
+4096-graph batch is also split over the ranks (LPT by n^3, no collective) and
+timed as one job (max over ranks).
 """
 from __future__ import annotations
 
@@ -437,6 +439,41 @@ def bench_batched(torch, apsp, graphgen, args, dev):
             "note": "graph restore copy excluded (timed separately and subtracted)"}
 
 
+def bench_batched_sharded(torch, apsp, graphgen, args, dev, rank, world):
+    """The 4096-graph batch split over the ranks (LPT by n^3, no exchange on the
+    data path): this rank's share in one batched launch replayed from a CUDA
+    graph.  Returns this rank's seconds per launch and its share."""
+    import numpy as np
+    from paper_2105_07298_gb300 import batched, shard
+    sizes = graphgen.batch_sizes(4096, 16, 512, 1)
+    sh = shard.shards(sizes, world)[rank]
+    W = graphgen.batched_graphs_torch(sh.sizes, 0.3, 1, sh.offsets, sh.numel, graph_ids=sh.ids, device=dev)
+    D = torch.empty_like(W)
+    P = torch.empty(sh.numel, dtype=torch.int32, device=dev)
+    plan = batched.BatchedPlan(sh.sizes, sh.offsets)
+    D.copy_(W)
+    plan.run(D, P)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run(D, P)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        D.copy_(W)
+        g.replay()
+    torch.cuda.synchronize()
+    reps = 3
+    total = 0.0
+    for _ in range(reps):
+        D.copy_(W)
+        total += time_events(torch, g.replay)
+    plan.close()
+    return total / reps, {"graphs": int(len(sh.ids)), "relax": float(np.sum(sh.sizes.astype(np.float64) ** 3))}
+
+
 def bench_fwd_bwd(torch, apsp, graphgen, args, dev):
     import numpy as np
     from paper_2105_07298_gb300 import batched
@@ -632,6 +669,13 @@ def run_ours(args):
     }
 
     details = {}
+    if world > 1 and not args.no_extras and args.dtype == "f32":
+        t_shard, share = bench_batched_sharded(torch, apsp, graphgen, args, dev, rank, world)
+        t_job = reduce_max(t_shard, world, dev)
+        if rank == 0:
+            details["batched_sharded"] = {"graphs": 4096, "ranks": world, "split": "LPT by n^3, no collective",
+                                          "scaling": "strong", "ms": 1e3 * t_job, "graphs_per_s": 4096 / t_job,
+                                          "rank0_share": share}
     if rank == 0 and not args.no_extras and args.dtype == "f32":
         del D
         torch.cuda.empty_cache()
@@ -724,6 +768,9 @@ def summary_of(details, line):
         out["batched"] = {"graphs_per_s": round(b["graphs_per_s"]), "ms": round(b["ms"], 3),
                           "relax_per_s": float("%.4g" % b["relax_per_s"]), "frac": round(b["frac_of_unit_peak"], 4),
                           "vs_per_graph": round(b["speedup_vs_per_graph"], 1)}
+    bs = details.get("batched_sharded")
+    if bs:
+        out["batched_sharded"] = {"graphs_per_s": round(bs["graphs_per_s"]), "ranks": bs["ranks"]}
     fb = details.get("fwd_bwd")
     if fb:
         out["fwd_bwd_ms"] = round(fb["fwd_bwd_ms"], 3)

@@ -252,10 +252,12 @@ def random_tree_graph(n: int, seed: int, lo=0.5, hi=2.0, dtype=np.float64) -> tu
 
 
 def batched_graphs_torch(sizes, p: float, seed: int, offsets, total: int, *, weights: str = "int",
-                         lo: float = 1, hi: float = 100, device="cpu", dtype=None):
+                         lo: float = 1, hi: float = 100, device="cpu", dtype=None, graph_ids=None):
     """All graphs of :func:`batched_graphs` drawn at once with torch into one packed
     buffer of ``total`` elements (graph g at element offsets[g]); element values are
-    identical to the numpy draw (same per-graph seeds and hashes)."""
+    identical to the numpy draw (same per-graph seeds and hashes).  ``graph_ids``
+    (optional) gives each entry's index in a larger batch, whose seed it then
+    uses (a rank drawing only its share of a batch)."""
     import torch
 
     dtype = dtype or torch.float32
@@ -263,7 +265,8 @@ def batched_graphs_torch(sizes, p: float, seed: int, offsets, total: int, *, wei
     out = torch.full((total,), float("nan"), dtype=dtype, device=device)
     if len(sizes) == 0:
         return out
-    keys = np.array([stream_keys(seed * 1000003 + g) for g in range(len(sizes))], dtype=np.int64)
+    ids = range(len(sizes)) if graph_ids is None else [int(g) for g in graph_ids]
+    keys = np.array([stream_keys(seed * 1000003 + g) for g in ids], dtype=np.int64)
     thr = min(int(round(p * 2.0 ** 32)), 1 << 32)
     M = torch.tensor(_M32, dtype=torch.int64, device=device)
 

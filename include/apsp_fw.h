@@ -77,7 +77,8 @@ int apsp_fw_block_size(int elem_bytes);
  *
  *   d_dist : n x n (leading dim ld) distances, overwritten in place:
  *            input = edge weights, output = shortest-path distances.
- *   n      : number of vertices, 0 <= n <= 65536 (n = 0 is a no-op).
+ *   n      : number of vertices, 0 <= n <= 262144 (n = 0 is a no-op); device
+ *            memory bounds it first (D and P of FP32 take 8 n^2 bytes).
  *   ld     : leading dimension in elements, ld >= max(n, 1).
  *   d_path : optional n x n int32 path matrix with the same ld; when non-NULL
  *            it is fully written (P as described above).  May be NULL.
@@ -90,7 +91,7 @@ int apsp_fw_block_size(int elem_bytes);
  *            Scratch (operand panels: about 32 n TB bytes for FP32, 96 n TB
  *            bytes for FP64; 128 MiB / 384 MiB at n = 32768) is stream-ordered
  *            (cudaMallocAsync / cudaFreeAsync on `stream`).
- * Returns APSP_OK, APSP_EINVAL (null d_dist with n > 0, ld < n, n > 65536),
+ * Returns APSP_OK, APSP_EINVAL (null d_dist with n > 0, ld < n, n > 262144),
  * APSP_ENOMEM (scratch) or APSP_ECUDA.
  * ---------------------------------------------------------------------- */
 int apsp_fw_f32(float *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);

@@ -68,6 +68,8 @@ def lib():
             L.oracle_fw_backward_f64.argtypes = [_p, _p, _p, _i64, _p]
             L.oracle_fw_backward_f64.restype = ctypes.c_int
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_minplus_rows_f32.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p]
+            L.oracle_minplus_rows_f32.restype = None
             _lib = L
     return _lib
 
@@ -137,6 +139,20 @@ def dijkstra_rows(W: np.ndarray, srcs) -> np.ndarray:
     return out
 
 
+def minplus_rows_accumulate(Drows: np.ndarray, Wchunk: np.ndarray, k0: int, best: np.ndarray) -> None:
+    """best[t, j] = min(best[t, j], min over chunk rows k != j of Drows[t, k] + W[k, j])
+    (float32 inputs, float64 accumulator, in place).  With best started at +inf
+    and every chunk of W fed once, a sampled row of exact distances from source
+    i has Drows[t, i] = 0 and Drows[t, j] == best[t, j] for all j != i (the
+    Bellman equations; positive weights)."""
+    Drows = np.ascontiguousarray(Drows, dtype=np.float32)
+    Wchunk = np.ascontiguousarray(Wchunk, dtype=np.float32)
+    s, n = Drows.shape
+    kc = Wchunk.shape[0]
+    assert Wchunk.shape[1] == n and best.shape == (s, n) and best.dtype == np.float64 and best.flags.c_contiguous
+    lib().oracle_minplus_rows_f32(_ptr(Drows), s, n, _ptr(Wchunk), int(k0), kc, _ptr(best))
+
+
 def bellman_ford(W: np.ndarray, src: int):
     """Single-source Bellman-Ford (any sign), fp64.  Returns (dist, has_negative_cycle)."""
     W64 = np.ascontiguousarray(W, dtype=np.float64)
@@ -155,6 +171,32 @@ def reconstruct_path(P: np.ndarray, i: int, j: int, max_len: int | None = None):
     buf = np.empty(max_len, dtype=np.int64)
     ln = lib().oracle_reconstruct_path(_ptr(P), ld, int(i), int(j), _ptr(buf), max_len)
     return None if ln < 0 else buf[:ln].tolist()
+
+
+def reconstruct_path_lookup(p_at, i: int, j: int, max_len: int):
+    """path(i, j) from a path matrix read one entry at a time (``p_at(a, c)`` returns
+    P[a][c]), for matrices too large to copy whole: path(a, c) = [a, c] when
+    P[a][c] = -1, else path(a, k) ++ path(k, c) with k = P[a][c].  Returns the
+    vertex list ([i] when i == j), or None if it does not end within max_len vertices."""
+    if i == j:
+        return [i]
+    out = [i]
+    stack = [j]
+    a = i
+    while stack:
+        c = stack[-1]
+        k = int(p_at(a, c))
+        if k < 0:
+            out.append(c)
+            stack.pop()
+            a = c
+            if len(out) > max_len:
+                return None
+        else:
+            if len(stack) > max_len:
+                return None
+            stack.append(k)
+    return out
 
 
 def fw_backward(gD: np.ndarray, P: np.ndarray, D: np.ndarray) -> np.ndarray:

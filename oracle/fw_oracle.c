@@ -274,6 +274,36 @@ EXPORT int oracle_fw_backward_f64(const double *gD, const int32_t *P, const doub
   return rc;
 }
 
+/* -------------------------------------------------------------------------
+ * Bellman equations of sampled distance rows, for sizes where no whole-matrix
+ * oracle fits in memory.  With positive weights and D[i][i] = 0, a row d is
+ * the exact shortest-distance row of source i iff for every j != i
+ *     d[j] = min over k != j of (d[k] + W[k][j])
+ * (d[j] cannot be improved by any edge, and is attained through a
+ * predecessor; by induction on d every finite d[j] is then the length of a
+ * real path).  This accumulates the right-hand side over a chunk of weight
+ * rows k0 .. k0+kc-1:
+ *     best[t][j] = min(best[t][j], min over k in the chunk, k != j, of
+ *                       Drows[t][k] + Wchunk[k - k0][j])      (in double)
+ * Drows is s x n, Wchunk kc x n, best s x n (float32 inputs).
+ * ------------------------------------------------------------------------- */
+EXPORT void oracle_minplus_rows_f32(const float *Drows, int64_t s, int64_t n, const float *Wchunk, int64_t k0,
+                                    int64_t kc, double *best) {
+  _Pragma("omp parallel for schedule(static)")
+  for (int64_t j = 0; j < n; ++j) {
+    for (int64_t t = 0; t < s; ++t) {
+      double b = best[t * n + j];
+      for (int64_t kk = 0; kk < kc; ++kk) {
+        const int64_t k = k0 + kk;
+        if (k == j) continue;
+        const double c = (double)Drows[t * n + k] + (double)Wchunk[kk * n + j];
+        if (c < b) b = c;
+      }
+      best[t * n + j] = b;
+    }
+  }
+}
+
 EXPORT int oracle_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -123,7 +123,7 @@ APSP_EXPORT int apsp_fw_backward_f32(const float *d_grad_dist, const int32_t *d_
   }
   if (!d_grad_dist || !d_path || !d_dist || !d_grad_w || ld < n) return APSP_EINVAL;
   if (batch > 1 && stride < n * ld) return APSP_EINVAL;
-  if (n > 65536) return APSP_EINVAL;
+  if (n > (1 << 18)) return APSP_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaGetLastError();
   if (d_status && cudaMemsetAsync(d_status, 0, 4, s) != cudaSuccess) return APSP_ECUDA;

@@ -181,6 +181,7 @@ constexpr int K1_THREADS = 512;
 struct K1Smem {
   double d[T * T];
   float dlo[T * T];
+  unsigned char pk[T * T];  // block-local k of the last improvement, 0xFF none
 };
 
 __global__ void __launch_bounds__(K1_THREADS, 1)
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     const double v = (i < m && j < m) ? D[(int64_t)(base + i) * ld + base + j] : INF;
     sm.d[e] = v;
     sm.dlo[e] = f64_down(v);
+    sm.pk[e] = 0xFF;
   }
   if (packA)
     for (int b = tid; b < R; b += K1_THREADS) {
@@ -203,14 +205,11 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
       packB[b].exact = 1;
     }
   __syncthreads();
-  float dhi[4][8];
-  unsigned pk[4][2];  // byte 4 (cb & 1) ... : block-local k of the last improvement, 0xFF none
+  // element t = 8 rr + c of this thread: i = ty + 32 rr, j = 2 tx + (c & 1) + 32 (c >> 1)
+  float dhi[32];
 #pragma unroll
-  for (int rr = 0; rr < 4; ++rr) {
-    pk[rr][0] = pk[rr][1] = 0xFFFFFFFFu;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) dhi[rr][c] = f64_up(sm.d[(ty + 32 * rr) * T + 2 * tx + (c & 1) + 32 * (c >> 1)]);
-  }
+  for (int t = 0; t < 32; ++t)
+    dhi[t] = f64_up(sm.d[(ty + 32 * (t >> 3)) * T + 2 * tx + (t & 1) + 32 * ((t & 7) >> 1)]);
 #pragma unroll 1
   for (int k = 0; k < m; ++k) {
     float alo[4];
@@ -219,43 +218,44 @@ __global__ void __launch_bounds__(K1_THREADS, 1)
     for (int rr = 0; rr < 4; ++rr) alo[rr] = sm.dlo[(ty + 32 * rr) * T + k];
 #pragma unroll
     for (int cb = 0; cb < 4; ++cb) blo[cb] = *reinterpret_cast<const unsigned long long *>(&sm.dlo[k * T + 2 * tx + 32 * cb]);
+    unsigned cand_mask = 0u;  // bit t: the candidate's lower bound is below element t's upper bound
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const unsigned long long aa = packf2(alo[rr], alo[rr]);
 #pragma unroll
       for (int cb = 0; cb < 4; ++cb) {
         const float2 lo = sum2_rm(aa, blo[cb]);
+        cand_mask |= (lo.x < dhi[8 * rr + 2 * cb] ? 1u : 0u) << (8 * rr + 2 * cb);
+        cand_mask |= (lo.y < dhi[8 * rr + 2 * cb + 1] ? 1u : 0u) << (8 * rr + 2 * cb + 1);
+      }
+    }
+    // The exact test, once per flagged element (rolled: the code stays small).
+#pragma unroll 1
+    while (cand_mask) {
+      const int t = __ffs(cand_mask) - 1;
+      cand_mask &= cand_mask - 1;
+      const int i = ty + 32 * (t >> 3), j = 2 * tx + (t & 1) + 32 * ((t & 7) >> 1);
+      const double cand = __dadd_rn(sm.d[i * T + k], sm.d[k * T + j]);
+      if (cand < sm.d[i * T + j]) {
+        sm.d[i * T + j] = cand;
+        sm.dlo[i * T + j] = f64_down(cand);
+        sm.pk[i * T + j] = (unsigned char)k;
+        const float up = f64_up(cand);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int c = 2 * cb + q;
-          if ((q ? lo.y : lo.x) < dhi[rr][c]) {
-            const int i = ty + 32 * rr, j = 2 * tx + q + 32 * cb;
-            const double cand = __dadd_rn(sm.d[i * T + k], sm.d[k * T + j]);
-            if (cand < sm.d[i * T + j]) {
-              sm.d[i * T + j] = cand;
-              sm.dlo[i * T + j] = f64_down(cand);
-              dhi[rr][c] = f64_up(cand);
-              pk[rr][cb >> 1] = __byte_perm(pk[rr][cb >> 1], (unsigned)k,
-                                            0x3210 ^ ((0x3210 & (0xF << (4 * (c & 3)))) ^ (4 << (4 * (c & 3)))));
-            }
-          }
-        }
+        for (int u = 0; u < 32; ++u) dhi[u] = u == t ? up : dhi[u];
       }
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int i = ty + 32 * rr, j = 2 * tx + (c & 1) + 32 * (c >> 1);
-      const unsigned kl = (pk[rr][c >> 2] >> (8 * (c & 3))) & 0xFFu;
-      if (kl != 0xFFu && i < m && j < m) {
-        const int64_t g = (int64_t)(base + i) * ld + base + j;
-        D[g] = sm.d[i * T + j];
-        if (P) P[g] = base + (int)kl;
-      }
+  for (int e = tid; e < T * T; e += K1_THREADS) {
+    const int i = e / T, j = e % T;
+    const unsigned kl = sm.pk[e];
+    if (kl != 0xFFu && i < m && j < m) {
+      const int64_t g = (int64_t)(base + i) * ld + base + j;
+      D[g] = sm.d[e];
+      if (P) P[g] = base + (int)kl;
     }
+  }
 }
 
 // ---------------------------------------------------------------- K2
@@ -321,41 +321,55 @@ __global__ void __launch_bounds__(k2::K2_THREADS, 2)
     }
   }
   __syncthreads();
-  // Step k: owner lane (k mod 64) / 2, slot 2 (k / 64) + (k mod 2).
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  // Step k: owner lane (k mod 64) / 2, slot 2 (k / 64) + (k mod 2).  The
+  // filter runs unrolled over the warp's lines; the exact FP64 tests run in a
+  // rolled loop over the flagged elements, so the loop body stays small.
 #pragma unroll 1
-    for (int kk = 0; kk < 32; ++kk) {
+  for (int k = 0; k < T; ++k) {
+    const int owner = (k & 63) >> 1, slot = 2 * (k >> 6) + (k & 1);
+    const unsigned long long m01 = *reinterpret_cast<const unsigned long long *>(&Mlo[k * MS + 2 * lane]);
+    const unsigned long long m23 = *reinterpret_cast<const unsigned long long *>(&Mlo[k * MS + 64 + 2 * lane]);
+    unsigned pass = 0u;  // bit 4 c + q
 #pragma unroll
-      for (int par = 0; par < 2; ++par) {
-        const int k = 64 * h + 2 * kk + par;
-        const unsigned long long m01 = *reinterpret_cast<const unsigned long long *>(&Mlo[k * MS + 2 * lane]);
-        const unsigned long long m23 = *reinterpret_cast<const unsigned long long *>(&Mlo[k * MS + 64 + 2 * lane]);
+    for (int c = 0; c < LINES; ++c) {
+      const float own_lo = slot == 0 ? vlo[c][0] : slot == 1 ? vlo[c][1] : slot == 2 ? vlo[c][2] : vlo[c][3];
+      const float vk_lo = __shfl_sync(kFullMask, own_lo, owner);
+      const unsigned long long vv = packf2(vk_lo, vk_lo);
+      const float2 l01 = sum2_rm(m01, vv), l23 = sum2_rm(m23, vv);
+      pass |= ((l01.x < vhi[c][0] ? 1u : 0u) | (l01.y < vhi[c][1] ? 2u : 0u) | (l23.x < vhi[c][2] ? 4u : 0u) |
+               (l23.y < vhi[c][3] ? 8u : 0u)) << (4 * c);
+    }
+    const unsigned any = __ballot_sync(kFullMask, pass != 0u);
+    if (!any) continue;  // warp-uniform
+    double vk[LINES];
 #pragma unroll
-        for (int c = 0; c < LINES; ++c) {
-          const float vk_lo = __shfl_sync(kFullMask, vlo[c][2 * h + par], kk);
-          const unsigned long long vv = packf2(vk_lo, vk_lo);
-          const float2 l01 = sum2_rm(m01, vv), l23 = sum2_rm(m23, vv);
-          const float lo[4] = {l01.x, l01.y, l23.x, l23.y};
-          unsigned pass = 0u;
+    for (int c = 0; c < LINES; ++c) {
+      const double own = slot == 0 ? v[c][0] : slot == 1 ? v[c][1] : slot == 2 ? v[c][2] : v[c][3];
+      vk[c] = __shfl_sync(kFullMask, own, owner);
+    }
+#pragma unroll 1
+    while (pass) {
+      const int b = __ffs(pass) - 1, c = b >> 2, q = b & 3;
+      pass &= pass - 1;
+      const int pos = 2 * lane + (q & 1) + 64 * (q >> 1);
+      double vkc = vk[0];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) pass |= (lo[q] < vhi[c][q] ? 1u : 0u) << q;
-          if (__any_sync(kFullMask, pass != 0u)) {
-            const double vk = __shfl_sync(kFullMask, v[c][2 * h + par], kk);
+      for (int u = 1; u < LINES; ++u) vkc = u == c ? vk[u] : vkc;
+      const double cand = __dadd_rn(__ldg(diag + pos * dpos + k * dk), vkc);
+      double cur = 0.0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (!((pass >> q) & 1u)) continue;
-              const int pos = 2 * lane + (q & 1) + 64 * (q >> 1);
-              const double cand = __dadd_rn(__ldg(diag + pos * dpos + k * dk), vk);
-              if (cand < v[c][q]) {
-                v[c][q] = cand;
-                vlo[c][q] = f64_down(cand);
-                vhi[c][q] = f64_up(cand);
-                pk[c] = __byte_perm(pk[c], (unsigned)k, 0x3210 ^ ((0x3210 & (0xF << (4 * q))) ^ (4 << (4 * q))));
-              }
-            }
+      for (int u = 0; u < 4 * LINES; ++u) cur = u == b ? v[u >> 2][u & 3] : cur;
+      if (cand < cur) {
+        const float lo = f64_down(cand), up = f64_up(cand);
+#pragma unroll
+        for (int u = 0; u < 4 * LINES; ++u)
+          if (u == b) {
+            v[u >> 2][u & 3] = cand;
+            vlo[u >> 2][u & 3] = lo;
+            vhi[u >> 2][u & 3] = up;
+            pk[u >> 2] = __byte_perm(pk[u >> 2], (unsigned)k,
+                                     0x3210 ^ ((0x3210 & (0xF << (4 * (u & 3)))) ^ (4 << (4 * (u & 3)))));
           }
-        }
       }
     }
   }

@@ -716,7 +716,10 @@ std::vector<cudaEvent_t> g_prof_pool;
 // --------------------------------------------------------------------------
 // Host side: argument checks and the round loop (all launches on `stream`).
 // --------------------------------------------------------------------------
-constexpr int kMaxN = 65536;
+// Largest n: vertex indices and block coordinates stay in 32-bit integers,
+// element offsets are 64-bit.  In practice device memory bounds n first
+// (FP32 D + P take 8 n^2 bytes: 128 GiB at n = 131072).
+constexpr int kMaxN = 1 << 18;
 
 constexpr int kT32 = mp32::T, kT64 = 128;
 static int g_smem_k1f[64], g_smem_p2f[64], g_smem_k3[64], g_smem_k3e[64];

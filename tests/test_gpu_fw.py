@@ -182,7 +182,7 @@ def test_argument_errors():
     assert lib.apsp_fw_f32(None, 4, 4, None, None) == apsp.APSP_EINVAL
     assert lib.apsp_fw_f32(x.data_ptr(), 4, 3, None, None) == apsp.APSP_EINVAL
     assert lib.apsp_fw_f32(x.data_ptr(), -1, 4, None, None) == apsp.APSP_EINVAL
-    assert lib.apsp_fw_f32(x.data_ptr(), 70000, 70000, None, None) == apsp.APSP_EINVAL
+    assert lib.apsp_fw_f32(x.data_ptr(), (1 << 18) + 1, (1 << 18) + 1, None, None) == apsp.APSP_EINVAL
     assert lib.apsp_fw_f32(None, 0, 0, None, None) == apsp.APSP_OK  # empty graph: no-op
     with pytest.raises(ValueError):
         apsp.apsp_fw_f32(x.t())  # columns not contiguous
@@ -324,3 +324,45 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
     assert apsp.device_status() == apsp.APSP_OK
     with pytest.raises(apsp.ApspError):
         apsp.wait_timeout_selftest(0)
+
+
+def test_n131072_sampled_rows_bellman_and_paths():
+    """n = 131072 (above the former 65536 cap; 1.7e10 elements, 64-bit element
+    offsets and 64-bit generator indices), edge probability 0.5, integer
+    weights, FP32 + path matrix (128 GiB on the device).  No whole-matrix oracle
+    fits, so sampled rows are checked against the Bellman equations (exact:
+    every sum is an integer below 2^24), streaming W in row chunks, and sampled
+    paths are walked on the device copy of P and summed against W."""
+    n, seed = 131072, 20210517
+    torch.cuda.empty_cache()
+    D = graphgen.dense_graph_torch(n, 0.5, seed, device=DEV)
+    P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.apsp_fw_f32(D, P)
+    assert apsp.device_status() == apsp.APSP_OK
+    srcs = np.random.default_rng(n).integers(0, n, 4)
+    rows = D[torch.as_tensor(srcs, device=DEV)].cpu().numpy()
+    best = np.full((len(srcs), n), np.inf)
+    chunk = 2048
+    for k0 in range(0, n, chunk):
+        Wc = graphgen.dense_graph_rows_torch(n, k0, min(n, k0 + chunk), 0.5, seed, device=DEV).cpu().numpy()
+        oracle.minplus_rows_accumulate(rows, Wc, k0, best)
+    for t, i in enumerate(srcs):
+        others = np.arange(n) != i
+        assert rows[t, i] == 0
+        np.testing.assert_array_equal(rows[t][others].astype(np.float64), best[t][others])
+    # sampled paths: P read entry by entry from the device, weights drawn per row
+    rng = np.random.default_rng(1)
+    w_rows = {}
+
+    def w_at(a, b):
+        if a not in w_rows:
+            w_rows[a] = graphgen.dense_graph_rows_torch(n, a, a + 1, 0.5, seed, device=DEV)[0].cpu().numpy()
+        return float(w_rows[a][b])
+
+    for t, i in enumerate(srcs):
+        for j in rng.integers(0, n, 10):
+            path = oracle.reconstruct_path_lookup(lambda a, c: P[a, c].item(), int(i), int(j), n + 1)
+            assert path is not None and path[0] == i and path[-1] == j
+            assert sum(w_at(a, b) for a, b in zip(path[:-1], path[1:])) == float(rows[t, j])
+    del D, P
+    torch.cuda.empty_cache()

@@ -322,3 +322,33 @@ def test_batched_generator_numpy_equals_torch():
     packed = graphgen.batched_graphs_torch(sizes, 0.3, 9, off, total).numpy()
     for g, m in enumerate(graphgen.batched_graphs(sizes, 0.3, 9)):
         np.testing.assert_array_equal(packed[off[g]:off[g] + m.size], m.reshape(-1))
+
+
+def test_bellman_row_check_accepts_exact_rows_and_rejects_planted_errors():
+    """The Bellman-equation row check (used at sizes no whole-matrix oracle fits)
+    accepts the rows of Dijkstra's distances and rejects a row with one entry
+    lowered or raised by 1."""
+    n = 257
+    W = graphgen.dense_graph(n, 0.3, 77)
+    srcs = [0, 100, 256]
+    rows = oracle.dijkstra_rows(W, srcs).astype(np.float32)
+
+    def check(R):
+        best = np.full((len(srcs), n), np.inf)
+        for k0 in range(0, n, 50):
+            oracle.minplus_rows_accumulate(R, W[k0:k0 + 50], k0, best)
+        return all(R[t, i] == 0 and np.array_equal(R[t][np.arange(n) != i], best[t][np.arange(n) != i])
+                   for t, i in enumerate(srcs))
+
+    assert check(rows)
+    for delta in (-1.0, 1.0):
+        bad = rows.copy()
+        bad[1, 7] += delta
+        assert not check(bad)
+
+
+def test_path_lookup_walk_matches_whole_matrix_walk():
+    W = graphgen.dense_graph(120, 0.2, 3)
+    D, P = oracle.fw(W)
+    for i, j in [(0, 5), (7, 119), (50, 50), (3, 99)]:
+        assert oracle.reconstruct_path_lookup(lambda a, c: P[a, c], i, j, 121) == oracle.reconstruct_path(P, i, j)
