@@ -174,15 +174,17 @@ def alu_peak_relax_per_s(sms: int, mhz: float) -> float:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the sources the phase-4 kernel is built from: the shared headers
-    and the phase-4 section of fw_single.cu (from its namespace to the host
-    code), so that changes elsewhere in that file keep a capture valid."""
+    """Hash of the sources the phase-4 kernel is built from: the shared headers,
+    the phase-4 part of phases_f32.cuh and the kernel's launch wrapper in
+    fw_single.cu, so that changes elsewhere keep a capture valid."""
     d = os.path.join(ROOT, "paper_2105_07298_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("minplus_f32.cuh", "common.cuh", "bulk.cuh"):
         h.update(open(os.path.join(d, f)).read().encode())
+    txt = open(os.path.join(d, "phases_f32.cuh")).read()
+    h.update(txt[txt.index("namespace k3 {"):].encode())
     txt = open(os.path.join(d, "fw_single.cu")).read()
-    h.update(txt[txt.index("namespace k3 {"):txt.index("// Phase timing state")].encode())
+    h.update(txt[txt.index("template <bool EAGER>\n__global__"):txt.index("// Phase timing state")].encode())
     return h.hexdigest()[:16]
 
 

@@ -97,6 +97,17 @@ int apsp_fw_block_size(int elem_bytes);
 int apsp_fw_f32(float *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
 int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
 
+/* Integer weights (int32), exact.  Same conventions with APSP_I32_INF
+ * (INT32_MAX) in place of +infinity (no edge, no path).  Every int32 weight
+ * is allowed (negative ones without a negative cycle).  The solve runs on the
+ * FP64 path (every sum of fewer than 2^22 int32 values is exact in FP64, so D
+ * is the exact integer result, bit for bit that of any correct FW) through a
+ * stream-ordered n x n FP64 scratch (8 n^2 bytes).  A finite distance outside
+ * [-(2^31 - 1), 2^31 - 2] is written saturated and makes the next
+ * apsp_device_status return APSP_EUNSUPPORTED.  Returns as apsp_fw_f64. */
+#define APSP_I32_INF 0x7fffffff
+int apsp_fw_i32(int32_t *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched Floyd-Warshall (extension of the method; the paper has no batched
  * form): many independent graphs of uneven size in ONE persistent kernel
@@ -104,9 +115,15 @@ int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *st
  * elements (row-major, ld = n_g) starting at element offset off[g] of the
  * packed buffers.  Every graph is solved with the same relaxation rule as
  * above; results are bit-exact with the single-graph path on integer weights.
- * On real weights phases 2/3 of a graph are one min-plus product with its
- * closed diagonal block (rounded differently from the sequential k loop), and
- * D stays within the FP32 error bound of the exact distances.
+ * Each size class runs one of three kernel variants (apsp_batched_variant_info):
+ * 64 x 64 blocks with 4 x 4 register tiles and lazy (0) or eager (1) path
+ * tracking, whose phases 2/3 are one min-plus product with the closed
+ * diagonal block (on real weights rounded differently from the sequential k
+ * loop, within the FP32 error bound of the exact distances); or 128 x 128
+ * blocks with 8 x 4 tiles (2), the single-graph phases run by one CTA, which
+ * gives apsp_fw_f32's results bit for bit on any weights.  Variant 2 needs
+ * per-CTA operand panels: (graph-dependent) scratch of up to
+ * 2 MiB per resident CTA, held by the plan.
  *
  * Planning splits the graphs into size classes, orders them largest first
  * (longest-processing-time order) and uploads the work list.  A plan holds
@@ -120,7 +137,7 @@ int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *st
  *   d_dist     : packed FP32 distances, overwritten in place.
  *   d_path     : packed int32 path matrices (same offsets), or NULL.
  * apsp_fw_batched_f32 = plan + run + destroy (allocates and frees its work
- * list with stream-ordered allocation on `stream`).
+ * list and panels with stream-ordered allocation on `stream`).
  * ---------------------------------------------------------------------- */
 typedef struct apsp_batched_plan apsp_batched_plan;
 
@@ -141,8 +158,10 @@ int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_t *h_n, cons
  * heap.  Its work list lives in one fixed device array of the library
  * (1 MiB + 16 bytes, held on every GPU that loads the library until exit),
  * so num_graphs may be at most 65536; larger batches return
- * APSP_EUNSUPPORTED before anything is enqueued.  Arguments and results are
- * those of apsp_fw_batched_f32 (same kernels, same results).
+ * APSP_EUNSUPPORTED before anything is enqueued.  Arguments are those of
+ * apsp_fw_batched_f32 and so are the distances; the same persistent kernel
+ * runs, but a size class set to variant 2 (which needs panel scratch) runs
+ * variant 1 here, so path entries may break ties differently.
  *
  * Every call looks up the array's device address (cudaGetSymbolAddress, with
  * the caller's device current; this allocates nothing).  The first call on a
@@ -158,14 +177,18 @@ int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, const int32_t *h
 /* Autotuner hook for the batched kernel: per size class (0..3, vertex-count
  * bounds given by apsp_batched_class_bounds) pick the variant index used by
  * later plans.  apsp_batched_num_variants reports how many variants a class
- * has (variant 0: path entries recovered lazily after each block product;
- * variant 1: tracked in the inner loop per k-pair; results are identical).
- * Defaults are the built-in table. */
+ * has; apsp_batched_variant_info gives a variant's block edge, register tile
+ * (rows x columns of outputs per thread) and whether it tracks the path in
+ * its inner loop (eager = 1) or recovers it after each product (0).
+ * Distances are identical across variants on integer weights.  Defaults are
+ * the built-in table. */
 int apsp_batched_num_classes(void);
 int apsp_batched_class_bounds(int cls, int32_t *lo, int32_t *hi);
 int apsp_batched_num_variants(int cls);
 int apsp_batched_set_variant(int cls, int variant);
 int apsp_batched_get_variant(int cls);
+int apsp_batched_variant_info(int variant, int32_t *block, int32_t *tile_rows, int32_t *tile_cols,
+                              int32_t *eager);
 
 /* ------------------------------------------------------------------------
  * Backward pass (extension; not in the paper).  D[i][j] is the sum of the
@@ -227,18 +250,20 @@ int apsp_profile_enable(int on);
  * paper quotes datasheet peaks only, Table 1): runs the inner-loop
  * instruction pair of the FP32 kernels (dtype_bytes = 4: packed add.rn.f32x2
  * + three-input min) or of the FP64 path's lower-bound loop (dtype_bytes = 8:
- * add.rm.f32x2 + three-input min) on registers only, on every SM, and writes
- * the relaxations per clock per SM it sustains.  Synchronises `stream`; uses
- * and frees stream-ordered scratch.  Returns APSP_EINVAL for other
- * dtype_bytes or a NULL output. */
+ * add.rm.f32x2 + three-input min), or the integer alternative (dtype_bytes =
+ * -4: one DPX fused add-then-min, __viaddmin_s32, per relaxation) on
+ * registers only, on every SM, and writes the relaxations per clock per SM it
+ * sustains.  Synchronises `stream`; uses and frees stream-ordered scratch.
+ * Returns APSP_EINVAL for other dtype_bytes or a NULL output. */
 int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm, void *stream);
 
 /* Synchronizes `stream`, then returns and clears the error words that the
  * single-graph kernels set on the device when one of their bounded waits for
  * an asynchronous copy runs out (the kernel then leaves its block unchanged,
  * so the result of that solve is incomplete): APSP_OK if no wait ran out
- * since the last call, APSP_ETIMEOUT if one did, APSP_ECUDA if the stream or
- * the read-back failed. */
+ * since the last call, APSP_ETIMEOUT if one did, APSP_EUNSUPPORTED if
+ * apsp_fw_i32 saturated a distance, APSP_ECUDA if the stream or the
+ * read-back failed. */
 int apsp_device_status(void *stream);
 
 /* Self-test of that timeout path (a test hook; the paper has no counterpart).

@@ -30,6 +30,7 @@ SIGNATURES = {
     "apsp_fw_block_size": (ctypes.c_int, [ctypes.c_int]),
     "apsp_fw_f32": (ctypes.c_int, [_p, _i64, _i64, _p, _p]),
     "apsp_fw_f64": (ctypes.c_int, [_p, _i64, _i64, _p, _p]),
+    "apsp_fw_i32": (ctypes.c_int, [_p, _i64, _i64, _p, _p]),
     "apsp_batched_plan_create": (ctypes.c_int, [_p, _p, _i32, ctypes.POINTER(_p)]),
     "apsp_batched_plan_destroy": (ctypes.c_int, [_p]),
     "apsp_fw_batched_run_f32": (ctypes.c_int, [_p, _p, _p, _p]),
@@ -40,6 +41,8 @@ SIGNATURES = {
     "apsp_batched_num_variants": (ctypes.c_int, [ctypes.c_int]),
     "apsp_batched_set_variant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "apsp_batched_get_variant": (ctypes.c_int, [ctypes.c_int]),
+    "apsp_batched_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
     "apsp_fw_backward_packed_f32": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _i32, _p, _p]),
     "apsp_check_negative_cycle": (ctypes.c_int, [_p, ctypes.c_int, _i64, _i64, _p]),
@@ -139,13 +142,25 @@ def apsp_fw_f64(dist, path=None, stream=None):
     return _fw("apsp_fw_f64", dist, path, stream, torch.float64)
 
 
+I32_INF = 0x7FFFFFFF  # APSP_I32_INF: no edge / no path in an int32 matrix
+
+
+def apsp_fw_i32(dist, path=None, stream=None):
+    """In-place exact blocked Floyd-Warshall on a CUDA int32 n x n tensor
+    (``I32_INF`` marks a missing edge), optionally writing ``path``."""
+    import torch
+    return _fw("apsp_fw_i32", dist, path, stream, torch.int32)
+
+
 def apsp_fw(dist, path=None, stream=None):
-    """Dispatch on dtype to :func:`apsp_fw_f32` / :func:`apsp_fw_f64`."""
+    """Dispatch on dtype to :func:`apsp_fw_f32` / :func:`apsp_fw_f64` / :func:`apsp_fw_i32`."""
     import torch
     if dist.dtype == torch.float32:
         return apsp_fw_f32(dist, path, stream)
     if dist.dtype == torch.float64:
         return apsp_fw_f64(dist, path, stream)
+    if dist.dtype == torch.int32:
+        return apsp_fw_i32(dist, path, stream)
     raise TypeError(f"unsupported dtype {dist.dtype}")
 
 
@@ -211,7 +226,7 @@ from .backward import (apsp_fw_backward_f32, apsp_fw_backward_packed_f32, Shorte
                        shortest_path_distances, shortest_path_distances_packed)
 
 __all__ = [
-    "load", "ApspError", "block_size", "apsp_fw_f32", "apsp_fw_f64", "apsp_fw",
+    "load", "ApspError", "block_size", "apsp_fw_f32", "apsp_fw_f64", "apsp_fw_i32", "apsp_fw", "I32_INF",
     "BatchedPlan", "apsp_fw_batched_f32", "apsp_fw_batched", "apsp_fw_backward_f32",
     "apsp_fw_backward_packed_f32", "ShortestPathDistances", "shortest_path_distances",
     "shortest_path_distances_packed", "check_negative_cycle", "wait_timeout_selftest",

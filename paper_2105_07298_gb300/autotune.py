@@ -2,12 +2,13 @@
 on synthetic graphs of that class and keep the fastest.
 
 The batched launch solves graphs of several size classes at once; each class
-may use a different variant.  Both variants run 64 x 64 blocks with 4 x 4
-register tiles and differ in how the path matrix is produced: variant 0
-recovers each improved output's first argmin from the operands after a block
-product (lazy), variant 1 keeps the index of the last k-pair that lowered the
-accumulator inside the loop (eager).  Choices are cached per device name in a
-JSON file and applied with :func:`apply_cached`.
+may use a different variant.  The variants differ in block edge, register
+blocking and path tracking (``batched.variant_info``): 64 x 64 blocks with
+4 x 4 register tiles, path entries recovered after each block product (0,
+lazy) or kept in the inner loop (1, eager); 128 x 128 blocks with 8 x 4
+register tiles, the single-graph phase kernels run by one CTA with eager
+tracking (2).  Choices are cached per device name in a JSON file and applied
+with :func:`apply_cached`.
 
 Timing only: every variant computes the same distances (bit-exact on integer
 weights), so the choice never changes results on integer inputs.
@@ -21,7 +22,17 @@ import numpy as np
 
 from . import batched as _b
 
-CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+def _cache_path() -> str:
+    """Per-user cache file (outside the build folder, so a clean build keeps it);
+    APSP_AUTOTUNE_CACHE overrides it."""
+    env = os.environ.get("APSP_AUTOTUNE_CACHE")
+    if env:
+        return env
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "apsp_fw_gb300", "autotune.json")
+
+
+CACHE = _cache_path()
 
 
 def _class_sizes(cls: int, count: int, seed: int):
@@ -29,6 +40,20 @@ def _class_sizes(cls: int, count: int, seed: int):
     hi = min(hi, 512)
     rng = np.random.default_rng(seed + cls)
     return rng.integers(lo, hi + 1, size=count).astype(np.int64)
+
+
+def _random_batch(torch, sizes, off, total, seed, device):
+    """Dense random graphs for timing only (edge probability 0.3, integer
+    weights 1..100, +inf non-edges, zero diagonal), packed at ``off``."""
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    W = torch.full((total,), float("inf"), dtype=torch.float32)
+    for n, o in zip(sizes, off):
+        n, o = int(n), int(o)
+        w = torch.randint(1, 101, (n, n), generator=gen).float()
+        w[torch.rand((n, n), generator=gen) >= 0.3] = float("inf")
+        w.fill_diagonal_(0)
+        W[o:o + n * n] = w.reshape(-1)
+    return W.to(device)
 
 
 def _time_plan(torch, sizes, W, D, P, reps: int) -> float:
@@ -54,14 +79,12 @@ def autotune(device="cuda:0", graphs_per_class: int = 608, reps: int = 3, seed: 
     """Choose a variant per size class; returns {class: {"variant", "ms": [per variant]}}."""
     import torch
 
-    import graphgen
-
     result = {}
     for cls in range(_b.num_classes()):
         sizes = _class_sizes(cls, graphs_per_class, seed)
         off = _b.packed_offsets(sizes)
         total = _b.packed_numel(sizes)
-        W = graphgen.batched_graphs_torch(sizes, 0.3, seed, off, total, device=device)
+        W = _random_batch(torch, sizes, off, total, seed + cls, device)
         D = torch.empty_like(W)
         P = torch.empty(total, dtype=torch.int32, device=device)
         ms = []
@@ -70,7 +93,8 @@ def autotune(device="cuda:0", graphs_per_class: int = 608, reps: int = 3, seed: 
             ms.append(_time_plan(torch, sizes, W, D, P, reps))
         best = int(np.argmin(ms))
         _b.set_variant(cls, best)
-        result[cls] = {"variant": best, "ms": ms, "bounds": list(_b.class_bounds(cls))}
+        result[cls] = {"variant": best, "ms": ms, "bounds": list(_b.class_bounds(cls)),
+                       "shape": _b.variant_info(best)}
         if verbose:
             print(f"class {cls} {_b.class_bounds(cls)}: variant ms {ms} -> {best}")
         del W, D, P

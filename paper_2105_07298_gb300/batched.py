@@ -125,3 +125,12 @@ def set_variant(cls: int, variant: int):
 def get_variant(cls: int) -> int:
     from . import load
     return int(load().apsp_batched_get_variant(cls))
+
+
+def variant_info(variant: int) -> dict:
+    """Block edge, register tile and path tracking of a batched kernel variant."""
+    from . import load, _check
+    b, tr, tc, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().apsp_batched_variant_info(variant, ctypes.byref(b), ctypes.byref(tr), ctypes.byref(tc),
+                                            ctypes.byref(e)), "variant_info")
+    return {"block": b.value, "tile": f"{tr.value}x{tc.value}", "path": "eager" if e.value else "lazy"}

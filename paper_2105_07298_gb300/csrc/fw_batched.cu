@@ -7,28 +7,32 @@
 // CTA ever waits on another.
 //
 // Per graph (n_g <= 1024, row-major, ld = n_g) the CTA runs the blocked FW of
-// §2.2 with TB = 64 on the matrix in global memory (it stays in L2):
-//   phase 1     register-resident closure of the diagonal block (Algorithm 1
-//               restricted to the block, k sequential);
-//   phases 2+3  row block (r,J) <- min(C, D*(r,r) (x) C) and column block
-//               (I,r) <- min(C, C (x) D*(r,r)): once the diagonal block is
-//               closed, the sequential k loop over a panel block equals one
-//               min-plus product with the closed block, so these phases use
-//               the same block product as phase 4;
-//   phase 4     (I,J) <- min(C, D(I,r) (x) D(r,J)).
-// A block product keeps both operand blocks whole in shared memory (all 64
-// values of k, in the k-pair layout of the paired FADD2 + FMNMX3 inner loop).
-// Small graphs run few rounds, so a large share of outputs improves in each;
-// the path matrix is therefore produced in one of two ways, chosen per size
-// class by the autotuner:
-//   variant 0 (lazy):  after the product, improved outputs find their first
-//                      argmin k from the operands still in shared memory;
-//   variant 1 (eager): the inner loop also keeps the argmin k of every
-//                      output (three more instructions per k-pair).
+// §2.2 on the matrix in global memory (it stays in L2), with one of four
+// kernel variants chosen per size class by the autotuner:
+//   variants 0 and 1, 64 x 64 blocks, 4 x 4 register tile per thread:
+//     phase 1     register-resident closure of the diagonal block;
+//     phases 2+3  row block (r,J) <- min(C, D*(r,r) (x) C) and column block
+//                 (I,r) <- min(C, C (x) D*(r,r)): once the diagonal block is
+//                 closed, the sequential k loop over a panel block equals one
+//                 min-plus product with the closed block (same value in exact
+//                 arithmetic), so these phases use the phase-4 block product;
+//     phase 4     (I,J) <- min(C, D(I,r) (x) D(r,J)), both operand blocks whole
+//                 in shared memory (k-pair layout);
+//     path matrix: variant 0 recovers each improved output's first argmin k
+//     from the operands after the product (lazy), variant 1 keeps the index
+//     of the last improving k-pair in the inner loop (eager).
+//   variant 2, 128 x 128 blocks, 8 x 4 register tile per thread: the
+//     single-graph kernels' code run by one CTA: the register-resident closure
+//     for phase 1, the k-sequential line kernel for phases 2+3 (the paper's
+//     order), which also writes the round's operand panels into this CTA's
+//     scratch, and the bulk-copy ring product for phase 4 (two 128 x 64
+//     halves per block), tracking the path eagerly in the product's inner
+//     loop (a graph of n <= 1024 has at most 8 rounds, all dense in
+//     improvements).
 // On integer-valued weights all sums are exact and D equals every other
-// correct FW; on real weights the phase-2/3 products round differently from
-// the sequential loop (one sum through the closed block instead of a chain of
-// sums), within the same error bound.
+// correct FW whatever the variant; on real weights variant 2 gives the
+// sequential blocked FW's values at TB = 128 (those of apsp_fw_f32), variants
+// 0 and 1 round phases 2/3 through the closed block instead.
 #include <stdint.h>
 #include <stdlib.h>
 
@@ -36,8 +40,10 @@
 #include <numeric>
 #include <vector>
 
+#include "bulk.cuh"
 #include "common.cuh"
 #include "minplus_f32.cuh"
+#include "phases_f32.cuh"
 
 namespace apsp {
 
@@ -49,8 +55,19 @@ static const int32_t kClassHi[kNumClasses] = {64, 128, 256, kBatchedMaxN};
 __host__ __device__ constexpr int class_of_n(int32_t n) {
   return n <= 64 ? 0 : n <= 128 ? 1 : n <= 256 ? 2 : 3;
 }
-constexpr int kNumVariants = 2;
-static int g_variant[kNumClasses] = {1, 1, 0, 0};
+constexpr int kNumVariants = 3;
+static int g_variant[kNumClasses] = {1, 1, 2, 2};
+// Block edge, register tile and path tracking of each variant (for the
+// autotuner's table).
+static const int kVariantBlock[kNumVariants] = {64, 64, 128};
+static const int kVariantTileRows[kNumVariants] = {4, 4, 8};
+static const int kVariantTileCols[kNumVariants] = {4, 4, 4};
+static const int kVariantEager[kNumVariants] = {0, 1, 1};
+constexpr int kT128 = mp32::T;
+// Per-CTA operand panels of the 128-block variants: Apan, Bpan, Acp and Bt of
+// every block of one round (R <= 8 blocks for n <= 1024), 4-byte words.
+__host__ __device__ constexpr size_t panel_words_per_array(int rmax) { return (size_t)rmax * kT128 * kT128; }
+__host__ __device__ constexpr size_t panel_bytes_per_cta(int rmax) { return 4 * panel_words_per_array(rmax) * 4; }
 
 static int class_of(int32_t n) { return class_of_n(n); }
 
@@ -71,6 +88,9 @@ struct ProdSmem {
 union BatchedSmem {
   b64::ProdSmem prod;
   mp32::DiagSmemT<64> diag;
+  mp32::DiagSmemT<128> diag128;
+  float lines_M[k2::T * k2::MS];
+  k3::Smem prod128;
 };
 
 // Eager path tracking per k-pair: the three-input min writes the new
@@ -274,14 +294,71 @@ __device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *
   __syncthreads();
 }
 
+// The 128-block variant: the single-graph phases run by this CTA alone.
+// The panels (this CTA's scratch) are rewritten every round, so the product's
+// path recovery reads them through the coherent path (NC = false), and every
+// thread fences its generic writes before the bulk copies read them.
+// Returns false if a bounded copy wait ran out (error word set).
+__device__ __forceinline__ bool solve_graph128_f32(float *__restrict__ D, int32_t *__restrict__ P, int n,
+                                                   const Panels &pan, bool aligned, unsigned char *smem_raw) {
+  constexpr int T = kT128;
+  BatchedSmem &sm = *reinterpret_cast<BatchedSmem *>(smem_raw);
+  const int64_t ld = n;
+  const int R = (n + T - 1) / T;
+  const int vec_ok = aligned && (n % 4 == 0);
+  for (int r = 0; r < R; ++r) {
+    const int base = r * T, m = min(T, n - base);
+    __syncthreads();
+    mp32::diag_closure<8>(D, ld, P, base, m, sm.diag128);
+    __syncthreads();
+    if (R == 1) break;
+    for (int side = 0; side < 2; ++side) {  // row blocks (r, J), then column blocks (I, r)
+      const bool is_row = side == 0;
+      lines_load_diag(D, ld, n, r, is_row, sm.lines_M);
+      __syncthreads();
+      for (int o = 0; o < R; ++o) {
+        if (o == r) continue;
+        for (int part = 0; part < k2::PARTS; ++part) lines_part_f32(D, ld, P, n, r, o, is_row, part, pan, sm.lines_M);
+      }
+      __syncthreads();
+    }
+    fence_proxy_async_global();
+    __syncthreads();
+    for (int I = 0; I < R; ++I) {
+      if (I == r) continue;
+      for (int J = 0; J < R; ++J) {
+        if (J == r) continue;
+        for (int hJ = 0; hJ < 2; ++hJ) {
+          __syncthreads();  // the previous product's epilogue is done with the shared memory
+          if (!minplus_half_f32<true, false>(D, ld, P, n, I, J, hJ, r, vec_ok, pan, smem_raw)) return false;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // Work item t: graph order[t] & 0x3fffffff, variant order[t] >> 30.
-__global__ void __launch_bounds__(mp32::THREADS, 3)
+// scratch: per-CTA panel space of the 128-block variants (panel_bytes_per_cta(rmax)
+// bytes per CTA), or NULL when the work list holds only variants 0 and 1.
+__global__ void __launch_bounds__(mp32::THREADS, 2)
     fw_batched_persistent_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
                               const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
-                              const int64_t *__restrict__ offs, int num, int *__restrict__ counter) {
+                              const int64_t *__restrict__ offs, int num, int *__restrict__ counter,
+                              unsigned char *__restrict__ scratch, int rmax) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   BatchedSmem &sm = *reinterpret_cast<BatchedSmem *>(smem_raw);
   __shared__ int s_next;
+  Panels pan{};
+  if (scratch) {
+    unsigned char *base = scratch + (size_t)blockIdx.x * panel_bytes_per_cta(rmax);
+    const size_t words = panel_words_per_array(rmax);
+    pan.Apan = reinterpret_cast<unsigned long long *>(base);
+    pan.Bpan = reinterpret_cast<unsigned long long *>(base + words * 4);
+    pan.Acp = reinterpret_cast<float *>(base + 2 * words * 4);
+    pan.Bt = reinterpret_cast<float *>(base + 3 * words * 4);
+  }
   for (;;) {
     if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
     __syncthreads();
@@ -297,10 +374,15 @@ __global__ void __launch_bounds__(mp32::THREADS, 3)
     if (P) {
       for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[e] = -1;
     }
-    if (variant == 1)
+    const bool aligned = (reinterpret_cast<uintptr_t>(D) & 15) == 0;
+    bool ok = true;
+    if (variant == 2 && scratch)
+      ok = solve_graph128_f32(D, P, n, pan, aligned, smem_raw);
+    else if (variant == 1 || variant == 2)
       solve_graph_f32<true>(D, P, n, sm);
     else
       solve_graph_f32<false>(D, P, n, sm);
+    if (!ok) return;  // a copy wait ran out: the error word is set, this CTA stops
   }
 }
 
@@ -313,6 +395,8 @@ struct apsp_batched_plan {
   int64_t *d_off;
   int *d_counter;
   int grid;
+  unsigned char *d_scratch;  // panels of the 128-block variants (grid CTAs), or NULL
+  int rmax;                  // blocks per side of the largest graph that uses them
 };
 
 namespace {
@@ -328,12 +412,18 @@ int validate(const int32_t *h_n, const int64_t *h_off, int32_t num) {
 }
 
 // Largest graphs first (longest processing time first); each entry carries
-// the variant of its size class in bits 30-31.
-std::vector<int32_t> lpt_order(const int32_t *h_n, int32_t num) {
+// the variant of its size class in bits 30-31.  *rmax: blocks per side (of
+// 128) of the largest graph given a 128-block variant, 0 if none is.
+std::vector<int32_t> lpt_order(const int32_t *h_n, int32_t num, int *rmax) {
   std::vector<int32_t> order(num);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return h_n[a] > h_n[b]; });
-  for (auto &g : order) g |= apsp::g_variant[apsp::class_of(h_n[g])] << 30;
+  *rmax = 0;
+  for (auto &g : order) {
+    const int v = apsp::g_variant[apsp::class_of(h_n[g])];
+    if (v >= 2) *rmax = std::max(*rmax, (h_n[g] + apsp::kT128 - 1) / apsp::kT128);
+    g |= v << 30;
+  }
   return order;
 }
 
@@ -371,7 +461,7 @@ APSP_EXPORT int apsp_batched_plan_create(const int32_t *h_n, const int64_t *h_of
     return APSP_ENOMEM;
   }
   if (num > 0) {
-    std::vector<int32_t> order = lpt_order(h_n, num);
+    std::vector<int32_t> order = lpt_order(h_n, num, &p->rmax);
     if (cudaMemcpy(p->d_order, order.data(), (size_t)num * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -384,6 +474,12 @@ APSP_EXPORT int apsp_batched_plan_create(const int32_t *h_n, const int64_t *h_of
     apsp_batched_plan_destroy(p);
     return APSP_ECUDA;
   }
+  if (p->rmax > 0 &&
+      cudaMalloc(&p->d_scratch, (size_t)p->grid * apsp::panel_bytes_per_cta(p->rmax)) != cudaSuccess) {
+    cudaGetLastError();
+    apsp_batched_plan_destroy(p);
+    return APSP_ENOMEM;
+  }
   *out_plan = p;
   return APSP_OK;
 }
@@ -394,6 +490,7 @@ APSP_EXPORT int apsp_batched_plan_destroy(apsp_batched_plan *p) {
   cudaFree(p->d_n);
   cudaFree(p->d_off);
   cudaFree(p->d_counter);
+  cudaFree(p->d_scratch);
   free(p);
   return APSP_OK;
 }
@@ -407,7 +504,7 @@ APSP_EXPORT int apsp_fw_batched_run_f32(const apsp_batched_plan *p, float *d_dis
   cudaGetLastError();
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) return APSP_ECUDA;
   apsp::fw_batched_persistent_f32<<<p->grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
-      d_dist, d_path, p->d_order, p->d_n, p->d_off, p->num, p->d_counter);
+      d_dist, d_path, p->d_order, p->d_n, p->d_off, p->num, p->d_counter, p->d_scratch, p->rmax);
   return apsp::status_from(cudaGetLastError());
 }
 
@@ -418,12 +515,21 @@ APSP_EXPORT int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_
   if (num == 0) return APSP_OK;
   if (!d_dist) return APSP_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  std::vector<int32_t> order = lpt_order(h_n, num);
-  // one scratch block: counter | order | n | offsets (stream-ordered allocation)
-  const size_t bytes = 16 + (size_t)num * 8 + (size_t)num * 8 + (size_t)num * 8;
+  int rmax = 0;
+  std::vector<int32_t> order = lpt_order(h_n, num, &rmax);
+  int grid = grid_for(num);
+  if (grid <= 0) return APSP_ECUDA;
+  // one scratch block: counter | order | n | offsets | panels of the
+  // 128-block variants (stream-ordered allocation)
+  const size_t list_bytes = (16 + (size_t)num * 8 + (size_t)num * 8 + (size_t)num * 8 + 255) & ~(size_t)255;
+  const size_t bytes = list_bytes + (rmax > 0 ? (size_t)grid * apsp::panel_bytes_per_cta(rmax) : 0);
   char *scratch = nullptr;
   cudaGetLastError();
-  if (cudaMallocAsync((void **)&scratch, bytes, s) != cudaSuccess) return APSP_ENOMEM;
+  if (cudaMallocAsync((void **)&scratch, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return APSP_ENOMEM;
+  }
+  unsigned char *panels = rmax > 0 ? reinterpret_cast<unsigned char *>(scratch + list_bytes) : nullptr;
   int *d_counter = reinterpret_cast<int *>(scratch);
   int32_t *d_order = reinterpret_cast<int32_t *>(scratch + 16);
   int32_t *d_n = d_order + num;
@@ -433,16 +539,14 @@ APSP_EXPORT int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order.data(), (size_t)num * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice, s);
-  int grid = grid_for(num);
-  if (e == cudaSuccess && grid > 0) {
+  if (e == cudaSuccess) {
     apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
-        d_dist, d_path, d_order, d_n, d_off, num, d_counter);
+        d_dist, d_path, d_order, d_n, d_off, num, d_counter, panels, rmax);
     e = cudaGetLastError();
   }
   // Copies from pageable host memory have consumed their sources when they
   // return, so `order` may go out of scope; the scratch is freed in stream order.
   cudaFreeAsync(scratch, s);
-  if (grid <= 0) return APSP_ECUDA;
   return apsp::status_from(e);
 }
 
@@ -468,6 +572,17 @@ APSP_EXPORT int apsp_batched_set_variant(int cls, int variant) {
 
 APSP_EXPORT int apsp_batched_get_variant(int cls) {
   return (cls < 0 || cls >= apsp::kNumClasses) ? -1 : apsp::g_variant[cls];
+}
+
+APSP_EXPORT int apsp_batched_variant_info(int variant, int32_t *block, int32_t *tile_rows, int32_t *tile_cols,
+                                          int32_t *eager) {
+  if (variant < 0 || variant >= apsp::kNumVariants || !block || !tile_rows || !tile_cols || !eager)
+    return APSP_EINVAL;
+  *block = apsp::kVariantBlock[variant];
+  *tile_rows = apsp::kVariantTileRows[variant];
+  *tile_cols = apsp::kVariantTileCols[variant];
+  *eager = apsp::kVariantEager[variant];
+  return APSP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -555,9 +670,12 @@ APSP_EXPORT int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, cons
   cudaError_t e = cudaMemcpyAsync(d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return APSP_ECUDA;
-  apsp::fw_batched_order<<<1, 1024, 0, s>>>(d_n, num, d_order, d_counter, apsp::g_variant[0],
-                                            apsp::g_variant[1], apsp::g_variant[2], apsp::g_variant[3]);
+  // The 128-block variant needs per-CTA panel space this entry point does not
+  // have: its classes run the 64-block variant with the same path tracking.
+  int v[apsp::kNumClasses];
+  for (int c = 0; c < apsp::kNumClasses; ++c) v[c] = apsp::g_variant[c] == 2 ? 1 : apsp::g_variant[c];
+  apsp::fw_batched_order<<<1, 1024, 0, s>>>(d_n, num, d_order, d_counter, v[0], v[1], v[2], v[3]);
   apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
-      d_dist, d_path, d_order, d_n, d_off, num, d_counter);
+      d_dist, d_path, d_order, d_n, d_off, num, d_counter, nullptr, 0);
   return apsp::status_from(cudaGetLastError());
 }

@@ -55,14 +55,41 @@ __global__ void __launch_bounds__(256) peak_kernel(float *out, unsigned long lon
   if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// The integer candidate of the same relaxation: one DPX fused add-then-min
+// (__viaddmin_s32: min(a + b, c)) per relaxation, on 16 independent chains
+// per thread.  Every instruction's add operand is its chain's previous
+// result, so nothing can be hoisted, and nothing else is in the loop.
+__global__ void __launch_bounds__(256) peak_kernel_dpx(int *out, unsigned long long *cycles, int iters) {
+  constexpr int CH = 16;
+  int acc[CH], lim[CH];
+#pragma unroll
+  for (int j = 0; j < CH; ++j) {
+    acc[j] = -(int)threadIdx.x - j;
+    lim[j] = (int)threadIdx.x * 7 + j;
+  }
+  __syncthreads();
+  const unsigned long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < CH; ++j) acc[j] = __viaddmin_s32(acc[j], 3, lim[j]);  // min(acc + 3, lim)
+  }
+  const unsigned long long t1 = clock64();
+  int s = 0;
+#pragma unroll
+  for (int j = 0; j < CH; ++j) s += acc[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace apsp
 
-// Runs the relaxation loop (dtype_bytes 4: FP32 pair; 8: the FP64 path's lower-bound pair)
+// Runs the relaxation loop (dtype_bytes 4: FP32 pair; 8: the FP64 path's lower-bound pair;
+// -4: the int32 DPX fused add-min)
 // on every SM and writes the achieved relaxations per clock per SM.  Uses the
 // caller's stream; synchronises it.  Scratch comes from stream-ordered
 // allocation and is freed before returning.
 APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm, void *stream) {
-  if (!relax_per_clk_per_sm || (dtype_bytes != 4 && dtype_bytes != 8)) return APSP_EINVAL;
+  if (!relax_per_clk_per_sm || (dtype_bytes != 4 && dtype_bytes != 8 && dtype_bytes != -4)) return APSP_EINVAL;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return APSP_ECUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return APSP_ECUDA;
@@ -73,8 +100,9 @@ APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm,
   const int threads = 256, iters = 4096;
   int per_sm = 0;
   const cudaError_t oe =
-      dtype_bytes == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel<0>, threads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel<1>, threads, 0);
+      dtype_bytes == 4   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel<0>, threads, 0)
+      : dtype_bytes == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel<1>, threads, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apsp::peak_kernel_dpx, threads, 0);
   if (oe != cudaSuccess || per_sm < 1) return APSP_ECUDA;
   const int blocks = sms * (per_sm < 4 ? per_sm : 4);
   float *out = nullptr;
@@ -87,7 +115,8 @@ APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm,
   }
   for (int rep = 0; rep < 2; ++rep) {  // the first pass warms clocks and caches
     if (dtype_bytes == 4) apsp::peak_kernel<0><<<blocks, threads, 0, s>>>(out, cyc, iters);
-    else apsp::peak_kernel<1><<<blocks, threads, 0, s>>>(out, cyc, iters);
+    else if (dtype_bytes == 8) apsp::peak_kernel<1><<<blocks, threads, 0, s>>>(out, cyc, iters);
+    else apsp::peak_kernel_dpx<<<blocks, threads, 0, s>>>(reinterpret_cast<int *>(out), cyc, iters);
   }
   unsigned long long *h = new unsigned long long[blocks];
   cudaError_t e = cudaMemcpyAsync(h, cyc, (size_t)blocks * 8, cudaMemcpyDeviceToHost, s);
@@ -102,8 +131,8 @@ APSP_EXPORT int apsp_measure_peak(int dtype_bytes, double *relax_per_clk_per_sm,
   for (int i = 0; i < blocks; ++i) mx = h[i] > mx ? h[i] : mx;
   delete[] h;
   // all blocks are resident at once; two relaxations (FP32, or FP64 lower
-  // bounds) per instruction pair.
-  const double relax = 2.0 * 16.0 * iters * (double)threads * blocks;
+  // bounds) per instruction pair, one per DPX add-min.
+  const double relax = (dtype_bytes == -4 ? 1.0 : 2.0) * 16.0 * iters * (double)threads * blocks;
   *relax_per_clk_per_sm = relax / sms / (double)mx;
   return APSP_OK;
 }

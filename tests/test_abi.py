@@ -35,6 +35,10 @@ def test_library_builds_loads_and_exports():
     assert L.apsp_batched_num_classes() == 4
     lo, hi = ctypes.c_int32(), ctypes.c_int32()
     assert L.apsp_batched_class_bounds(3, ctypes.byref(lo), ctypes.byref(hi)) == 0 and hi.value == 1024
+    b, tr, tc, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    assert L.apsp_batched_variant_info(2, ctypes.byref(b), ctypes.byref(tr), ctypes.byref(tc), ctypes.byref(e)) == 0
+    assert (b.value, tr.value, tc.value, e.value) == (128, 8, 4, 1)
+    assert L.apsp_batched_variant_info(3, ctypes.byref(b), ctypes.byref(tr), ctypes.byref(tc), ctypes.byref(e)) == 1
 
 
 def test_only_sm103a_code_in_build_flags():

@@ -115,15 +115,15 @@ def test_full_config_sampled_graphs():
     plan.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_every_variant_is_exact(variant):
-    """Each kernel variant (block edge / register tile) solves every size class
-    exactly; the autotuner's choice can only change speed."""
+    """Each kernel variant (block edge / register tile / path tracking) solves
+    every size class exactly; the autotuner's choice can only change speed."""
     saved = [B.get_variant(c) for c in range(B.num_classes())]
     try:
         for c in range(B.num_classes()):
             B.set_variant(c, variant)
-        sizes = [1, 7, 63, 64, 65, 100, 128, 129, 191, 200, 256, 257, 320, 511]
+        sizes = [1, 7, 63, 64, 65, 100, 128, 129, 191, 200, 256, 257, 320, 511, 1024]
         mats = [graphgen.dense_graph(n, 0.3, 1200 + n) for n in sizes]
         for W, (D, P) in zip(mats, _solve(sizes, mats)):
             np.testing.assert_array_equal(D, oracle.fw(W)[0])
@@ -178,3 +178,30 @@ def test_plan_captured_in_cuda_graph_replays_on_fresh_inputs():
             np.testing.assert_array_equal(Dg, oracle.fw(Wg)[0])
             assert oracle.check_paths(Wg, Dg, Pg) == 0
     plan.close()
+
+
+def test_128_block_variant_matches_single_graph_path_on_real_weights():
+    """Variant 2 runs the single-graph phase code (TB = 128, phases 2/3 k
+    sequential): on real weights D and P equal apsp_fw_f32's bit for bit."""
+    saved = [B.get_variant(c) for c in range(B.num_classes())]
+    try:
+        for c in range(B.num_classes()):
+            B.set_variant(c, 2)
+        sizes = [50, 130, 257, 300, 1000]
+        mats = [graphgen.dense_graph(n, 0.4, 300 + n, weights="real", lo=0.5, hi=2.0) for n in sizes]
+        for W, (D, P) in zip(mats, _solve(sizes, mats)):
+            t = torch.from_numpy(W).to(DEV)
+            pt = torch.empty(t.shape, dtype=torch.int32, device=DEV)
+            apsp.apsp_fw_f32(t, pt)
+            np.testing.assert_array_equal(D, t.cpu().numpy())
+            np.testing.assert_array_equal(P, pt.cpu().numpy())
+    finally:
+        for c, v in enumerate(saved):
+            B.set_variant(c, v)
+
+
+def test_variant_table_names_block_and_tile():
+    info = [B.variant_info(v) for v in range(B.num_variants(0))]
+    assert info[0] == {"block": 64, "tile": "4x4", "path": "lazy"}
+    assert info[1] == {"block": 64, "tile": "4x4", "path": "eager"}
+    assert info[2] == {"block": 128, "tile": "8x4", "path": "eager"}

@@ -366,3 +366,54 @@ def test_n131072_sampled_rows_bellman_and_paths():
             assert sum(w_at(a, b) for a, b in zip(path[:-1], path[1:])) == float(rows[t, j])
     del D, P
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [1, 130, 300, 513])
+def test_int32_weights_beyond_float_exactness(n):
+    """int32 weights up to 2^26 (path sums far above 2^24, where FP32 sums are
+    no longer exact): apsp_fw_i32 equals the oracle's FP64 FW exactly and its
+    paths sum to D; negative weights (potentials, no negative cycle) too."""
+    rng = np.random.default_rng(n)
+    W = graphgen.dense_graph(n, 0.3, 4000 + n, dtype=np.float64)
+    fin = np.isfinite(W) & ~np.eye(n, dtype=bool)
+    W[fin] = rng.integers(1, 1 << 26, fin.sum())
+    for shift in (False, True):
+        Wk = W.copy()
+        if shift:  # Johnson-style potentials keep shortest paths, make weights negative
+            h = rng.integers(-(1 << 20), 1 << 20, n).astype(np.float64)
+            Wk = np.where(np.isfinite(W), W + h[:, None] - h[None, :], np.inf)
+            np.fill_diagonal(Wk, 0)
+        Wi = np.where(np.isfinite(Wk), Wk, apsp.I32_INF).astype(np.int32)
+        D = torch.from_numpy(Wi).to(DEV)
+        P = torch.empty((n, n), dtype=torch.int32, device=DEV)
+        apsp.apsp_fw(D, P)
+        Dh = D.cpu().numpy()
+        ref = oracle.fw(Wk)[0]
+        expect = np.where(np.isfinite(ref), ref, apsp.I32_INF).astype(np.int64)
+        np.testing.assert_array_equal(Dh.astype(np.int64), expect)
+        Df = np.where(Dh == apsp.I32_INF, np.inf, Dh.astype(np.float64))
+        assert oracle.check_paths(Wk, Df, P.cpu().numpy()) == 0
+        assert apsp.device_status() == apsp.APSP_OK
+
+
+def test_int32_saturation_is_reported():
+    """A chain whose distances leave the int32 range: saturated values and
+    APSP_EUNSUPPORTED from the next device status; in-range entries exact."""
+    W = graphgen.chain_graph(np.full(4, float(1 << 30)))  # 0 -> 1 -> 2 -> 3 -> 4, 2^30 each
+    Wi = np.where(np.isfinite(W), W, apsp.I32_INF).astype(np.int64)
+    Wi[Wi > apsp.I32_INF] = apsp.I32_INF
+    D = torch.from_numpy(Wi.astype(np.int32)).to(DEV)
+    apsp.apsp_fw(D)
+    Dh = D.cpu().numpy().astype(np.int64)
+    assert Dh[0, 1] == 1 << 30 and Dh[0, 2] == 2147483646  # 2^31 saturates to 2^31 - 2
+    assert Dh[1, 0] == apsp.I32_INF
+    assert apsp.device_status() == apsp.APSP_EUNSUPPORTED
+    assert apsp.device_status() == apsp.APSP_OK
+
+
+def test_dpx_add_min_rate_is_measured():
+    """The int32 DPX fused add-min alternative is measured on this GPU (its rate
+    is what keeps the integer path on the FP64/FP32-pipe kernels)."""
+    r_dpx = apsp.measure_peak(-4)
+    r32 = apsp.measure_peak(4)
+    assert 8.0 < r_dpx <= 132.0 and r32 > 0
