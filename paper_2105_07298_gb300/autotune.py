@@ -98,6 +98,31 @@ def autotune(device="cuda:0", graphs_per_class: int = 608, reps: int = 3, seed: 
         if verbose:
             print(f"class {cls} {_b.class_bounds(cls)}: variant ms {ms} -> {best}")
         del W, D, P
+    # Variant 2 needs the two-CTAs-per-SM kernel, which every class then runs
+    # on: time the whole mixed batch with the per-class choices and with each
+    # variant-2 class set to its best 64-block variant, and keep the faster.
+    if any(r["variant"] == 2 for r in result.values()):
+        sizes = np.concatenate([_class_sizes(c, graphs_per_class // 2, seed + 100) for c in result])
+        off = _b.packed_offsets(sizes)
+        total = _b.packed_numel(sizes)
+        W = _random_batch(torch, sizes, off, total, seed + 100, device)
+        D = torch.empty_like(W)
+        P = torch.empty(total, dtype=torch.int32, device=device)
+        t_mixed = _time_plan(torch, sizes, W, D, P, reps)
+        alt = {c: (r["variant"] if r["variant"] != 2 else int(np.argmin(r["ms"][:2]))) for c, r in result.items()}
+        for c, v in alt.items():
+            _b.set_variant(c, v)
+        t_alt = _time_plan(torch, sizes, W, D, P, reps)
+        if t_alt <= t_mixed:
+            for c, v in alt.items():
+                result[c]["variant"] = v
+                result[c]["shape"] = _b.variant_info(v)
+        else:
+            for c, r in result.items():
+                _b.set_variant(c, r["variant"])
+        if verbose:
+            print(f"mixed batch: per-class choice {t_mixed:.3f} ms, without variant 2 {t_alt:.3f} ms")
+        del W, D, P
     if save:
         name = torch.cuda.get_device_name(torch.device(device))
         cache = {}

@@ -56,7 +56,7 @@ __host__ __device__ constexpr int class_of_n(int32_t n) {
   return n <= 64 ? 0 : n <= 128 ? 1 : n <= 256 ? 2 : 3;
 }
 constexpr int kNumVariants = 3;
-static int g_variant[kNumClasses] = {1, 1, 2, 2};
+static int g_variant[kNumClasses] = {1, 1, 1, 1};
 // Block edge, register tile and path tracking of each variant (for the
 // autotuner's table).
 static const int kVariantBlock[kNumVariants] = {64, 64, 128};
@@ -340,18 +340,20 @@ __device__ __forceinline__ bool solve_graph128_f32(float *__restrict__ D, int32_
 }
 
 // Work item t: graph order[t] & 0x3fffffff, variant order[t] >> 30.
-// scratch: per-CTA panel space of the 128-block variants (panel_bytes_per_cta(rmax)
-// bytes per CTA), or NULL when the work list holds only variants 0 and 1.
-__global__ void __launch_bounds__(mp32::THREADS, 2)
-    fw_batched_persistent_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
-                              const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
-                              const int64_t *__restrict__ offs, int num, int *__restrict__ counter,
-                              unsigned char *__restrict__ scratch, int rmax) {
+// scratch: per-CTA panel space of the 128-block variant (panel_bytes_per_cta(rmax)
+// bytes per CTA).  Two instances: the 64-block variants alone (three CTAs per
+// SM), and all variants (two CTAs per SM: the 128-block code needs more
+// registers); a plan launches the second only if some graph uses variant 2.
+template <bool WITH128>
+__device__ __forceinline__ void persistent_body(float *__restrict__ Dp, int32_t *__restrict__ Pp,
+                                                const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
+                                                const int64_t *__restrict__ offs, int num, int *__restrict__ counter,
+                                                unsigned char *__restrict__ scratch, int rmax) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   BatchedSmem &sm = *reinterpret_cast<BatchedSmem *>(smem_raw);
   __shared__ int s_next;
   Panels pan{};
-  if (scratch) {
+  if (WITH128 && scratch) {
     unsigned char *base = scratch + (size_t)blockIdx.x * panel_bytes_per_cta(rmax);
     const size_t words = panel_words_per_array(rmax);
     pan.Apan = reinterpret_cast<unsigned long long *>(base);
@@ -374,16 +376,36 @@ __global__ void __launch_bounds__(mp32::THREADS, 2)
     if (P) {
       for (int e = threadIdx.x; e < n * n; e += blockDim.x) P[e] = -1;
     }
-    const bool aligned = (reinterpret_cast<uintptr_t>(D) & 15) == 0;
     bool ok = true;
-    if (variant == 2 && scratch)
-      ok = solve_graph128_f32(D, P, n, pan, aligned, smem_raw);
-    else if (variant == 1 || variant == 2)
+    if constexpr (WITH128) {
+      if (variant == 2 && scratch) {
+        const bool aligned = (reinterpret_cast<uintptr_t>(D) & 15) == 0;
+        ok = solve_graph128_f32(D, P, n, pan, aligned, smem_raw);
+        if (!ok) return;  // a copy wait ran out: the error word is set, this CTA stops
+        continue;
+      }
+    }
+    if (variant == 1 || variant == 2)
       solve_graph_f32<true>(D, P, n, sm);
     else
       solve_graph_f32<false>(D, P, n, sm);
-    if (!ok) return;  // a copy wait ran out: the error word is set, this CTA stops
   }
+}
+
+__global__ void __launch_bounds__(mp32::THREADS, 3)
+    fw_batched_persistent_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
+                              const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
+                              const int64_t *__restrict__ offs, int num, int *__restrict__ counter,
+                              unsigned char *__restrict__ scratch, int rmax) {
+  persistent_body<false>(Dp, Pp, order, ns, offs, num, counter, scratch, rmax);
+}
+
+__global__ void __launch_bounds__(mp32::THREADS, 2)
+    fw_batched_persistent128_f32(float *__restrict__ Dp, int32_t *__restrict__ Pp,
+                                 const int32_t *__restrict__ order, const int32_t *__restrict__ ns,
+                                 const int64_t *__restrict__ offs, int num, int *__restrict__ counter,
+                                 unsigned char *__restrict__ scratch, int rmax) {
+  persistent_body<true>(Dp, Pp, order, ns, offs, num, counter, scratch, rmax);
 }
 
 }  // namespace apsp
@@ -427,17 +449,25 @@ std::vector<int32_t> lpt_order(const int32_t *h_n, int32_t num, int *rmax) {
   return order;
 }
 
-int g_smem_batched[64];
+int g_smem_batched[64], g_smem_batched128[64];
 
-int grid_for(int32_t num) {
+using PersistentKernel = void (*)(float *, int32_t *, const int32_t *, const int32_t *, const int64_t *, int, int *,
+                                  unsigned char *, int);
+
+PersistentKernel kernel_for(bool with128) {
+  return with128 ? apsp::fw_batched_persistent128_f32 : apsp::fw_batched_persistent_f32;
+}
+
+// Grid of the persistent launch: every SM filled with resident CTAs.
+int grid_for(int32_t num, bool with128) {
   int dev = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-  if (apsp::ensure_smem(apsp::fw_batched_persistent_f32, (int)sizeof(apsp::BatchedSmem), g_smem_batched))
+  const PersistentKernel k = kernel_for(with128);
+  if (apsp::ensure_smem(k, (int)sizeof(apsp::BatchedSmem), with128 ? g_smem_batched128 : g_smem_batched))
     return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apsp::fw_batched_persistent_f32,
-                                                    apsp::mp32::THREADS,
-                                                    sizeof(apsp::BatchedSmem)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem)) !=
+      cudaSuccess)
     return -1;
   const int g = sms * std::max(occ, 1);
   return std::max(1, std::min<int>(g, num));
@@ -469,7 +499,7 @@ APSP_EXPORT int apsp_batched_plan_create(const int32_t *h_n, const int64_t *h_of
       return APSP_ECUDA;
     }
   }
-  p->grid = grid_for(num);
+  p->grid = grid_for(num, p->rmax > 0);
   if (p->grid < 0) {
     apsp_batched_plan_destroy(p);
     return APSP_ECUDA;
@@ -503,7 +533,7 @@ APSP_EXPORT int apsp_fw_batched_run_f32(const apsp_batched_plan *p, float *d_dis
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaGetLastError();
   if (cudaMemsetAsync(p->d_counter, 0, sizeof(int), s) != cudaSuccess) return APSP_ECUDA;
-  apsp::fw_batched_persistent_f32<<<p->grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
+  kernel_for(p->rmax > 0)<<<p->grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
       d_dist, d_path, p->d_order, p->d_n, p->d_off, p->num, p->d_counter, p->d_scratch, p->rmax);
   return apsp::status_from(cudaGetLastError());
 }
@@ -517,7 +547,7 @@ APSP_EXPORT int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int rmax = 0;
   std::vector<int32_t> order = lpt_order(h_n, num, &rmax);
-  int grid = grid_for(num);
+  int grid = grid_for(num, rmax > 0);
   if (grid <= 0) return APSP_ECUDA;
   // one scratch block: counter | order | n | offsets | panels of the
   // 128-block variants (stream-ordered allocation)
@@ -540,7 +570,7 @@ APSP_EXPORT int apsp_fw_batched_f32(float *d_dist, int32_t *d_path, const int32_
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, h_off, (size_t)num * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
-    apsp::fw_batched_persistent_f32<<<grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
+    kernel_for(rmax > 0)<<<grid, apsp::mp32::THREADS, sizeof(apsp::BatchedSmem), s>>>(
         d_dist, d_path, d_order, d_n, d_off, num, d_counter, panels, rmax);
     e = cudaGetLastError();
   }
@@ -664,7 +694,7 @@ APSP_EXPORT int apsp_fw_batched_f32_noalloc(float *d_dist, int32_t *d_path, cons
   int32_t *d_n = d_order + apsp::kNoAllocMaxGraphs;
   int64_t *d_off = reinterpret_cast<int64_t *>(d_n + apsp::kNoAllocMaxGraphs);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int grid = grid_for(num);
+  const int grid = grid_for(num, false);
   if (grid <= 0) return APSP_ECUDA;
   cudaGetLastError();
   cudaError_t e = cudaMemcpyAsync(d_n, h_n, (size_t)num * 4, cudaMemcpyHostToDevice, s);

@@ -138,7 +138,12 @@ def test_autotuner_picks_a_variant_per_class():
     res = autotune.autotune(graphs_per_class=16, reps=1, save=False)
     assert set(res) == set(range(B.num_classes()))
     for c, r in res.items():
-        assert r["variant"] == int(np.argmin(r["ms"])) and B.get_variant(c) == r["variant"]
+        best = int(np.argmin(r["ms"]))
+        # the fastest per class, or (when a class's fastest needs the two-CTA
+        # kernel and the whole mixed batch ran faster without it) its best
+        # 64-block variant
+        assert r["variant"] == best or (best == 2 and r["variant"] == int(np.argmin(r["ms"][:2])))
+        assert B.get_variant(c) == r["variant"] and r["shape"] == B.variant_info(r["variant"])
 
 
 def test_plan_captured_in_cuda_graph_replays_on_fresh_inputs():
