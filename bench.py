@@ -175,14 +175,14 @@ def alu_peak_relax_per_s(sms: int, mhz: float) -> float:
 
 def kernel_source_hash() -> str:
     """Hash of the sources the phase-4 kernel is built from: the shared headers,
-    the phase-4 part of phases_f32.cuh and the kernel's launch wrapper in
-    fw_single.cu, so that changes elsewhere keep a capture valid."""
+    its constants and shared-memory layout (namespace k3 of phases_f32.cuh) and
+    the kernel in fw_single.cu, so that changes elsewhere keep a capture valid."""
     d = os.path.join(ROOT, "paper_2105_07298_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("minplus_f32.cuh", "common.cuh", "bulk.cuh"):
         h.update(open(os.path.join(d, f)).read().encode())
     txt = open(os.path.join(d, "phases_f32.cuh")).read()
-    h.update(txt[txt.index("namespace k3 {"):].encode())
+    h.update(txt[txt.index("namespace k3 {"):txt.index("}  // namespace k3")].encode())
     txt = open(os.path.join(d, "fw_single.cu")).read()
     h.update(txt[txt.index("template <bool EAGER>\n__global__"):txt.index("// Phase timing state")].encode())
     return h.hexdigest()[:16]
@@ -383,7 +383,8 @@ def bench_batched(torch, apsp, graphgen, args, dev):
     import numpy as np
     from paper_2105_07298_gb300 import batched
     from paper_2105_07298_gb300 import autotune
-    tuned = autotune.autotune(device=dev, graphs_per_class=304, reps=2, save=False)
+    tuned = ({} if args.no_autotune else
+             autotune.autotune(device=dev, graphs_per_class=304, reps=2, save=False))
     sizes = graphgen.batch_sizes(4096, 16, 512, 1)
     off = batched.packed_offsets(sizes)
     total = batched.packed_numel(sizes)
@@ -436,8 +437,9 @@ def bench_batched(torch, apsp, graphgen, args, dev):
             "frac_of_unit_peak": relax / t_solve / peak,
             "per_graph_launches": {"graphs_per_s": 4096 / t_pg, "ms": 1e3 * t_pg},
             "speedup_vs_per_graph": t_pg / t_solve,
-            "autotuned_variants": {str(c): {"variant": r["variant"], "bounds": r["bounds"],
+            "autotuned_variants": {str(c): {"variant": r["variant"], "bounds": r["bounds"], "shape": r["shape"],
                                             "ms_per_variant": r["ms"]} for c, r in tuned.items()},
+            "variants": [batched.get_variant(c) for c in range(batched.num_classes())],
             "note": "graph restore copy excluded (timed separately and subtracted)"}
 
 
@@ -576,6 +578,33 @@ def bench_sweep(torch, apsp, graphgen, args, dev, pair_rate=None):
                     "their own launches; n=4096 fits in L2"}
 
 
+def bench_sweep_f64(torch, apsp, graphgen, args, dev):
+    """FP64 blocked FW at the smaller sweep sizes, with the path matrix: solve
+    time (device events; input restored before each solve, outside the timed
+    region), relax/s and the fraction of the unit-count add+min peak (the FP64
+    main loop runs the FP32 pair on lower bounds)."""
+    facts = device_facts(torch)
+    max_mhz = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak_unit = alu_peak_relax_per_s(facts["sms"], max_mhz)
+    out = []
+    for n in args.sweep_f64:
+        W = graphgen.dense_graph_torch(n, 0.5, SEED, dtype=torch.float64, device=dev)
+        D = torch.empty_like(W)
+        P = torch.empty((n, n), dtype=torch.int32, device=dev)
+        D.copy_(W)
+        apsp.apsp_fw_f64(D, P)  # warm-up
+        reps = 3
+        total = 0.0
+        for _ in range(reps):
+            D.copy_(W)
+            total += time_events(torch, lambda: apsp.apsp_fw_f64(D, P))
+        t = total / reps
+        out.append({"n": n, "ms": 1e3 * t, "relax_per_s": n ** 3 / t, "frac_of_unit_peak": n ** 3 / t / peak_unit})
+        del W, D, P
+        torch.cuda.empty_cache()
+    return {"points": out, "dtype": "f64", "path_matrix": True}
+
+
 def run_side_workload(args, torch, apsp, graphgen, dev):
     """--workload batched / fwd_bwd: that measurement alone (profiling runs)."""
     if args.workload == "batched":
@@ -706,6 +735,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         if args.sweep:
             details["sweep"] = bench_sweep(torch, apsp, graphgen, args, dev, rate_meas)
+        if args.sweep_f64:
+            details["sweep_f64"] = bench_sweep_f64(torch, apsp, graphgen, args, dev)
         # CPU baseline: the oracle as it stands, bounded prefix of the same graph
         rate, k, thr, tcpu = oracle_partial_rate(Wh.numpy(), args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -777,6 +808,9 @@ def summary_of(details, line):
     if fb:
         out["fwd_bwd_ms"] = round(fb["fwd_bwd_ms"], 3)
         out["fwd_bwd_per_graph_ms"] = round(fb["per_graph_path"]["fwd_bwd_ms"], 2)
+    s64 = details.get("sweep_f64")
+    if s64:
+        out["sweep_f64_relax_per_s"] = {str(p["n"]): float("%.4g" % p["relax_per_s"]) for p in s64["points"]}
     sw = details.get("sweep")
     if sw:
         out["sweep_relax_per_s"] = {str(p["n"]): float("%.4g" % p["with_path"]["relax_per_s"]) for p in sw["points"]}
@@ -806,9 +840,13 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--gpu-index", default=None)
     ap.add_argument("--no-extras", action="store_true", help="only the FP32 timed steps")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched: keep the built-in variant table (deterministic launch order for profiling)")
     ap.add_argument("--sweep", type=lambda x: [int(v) for v in x.split(",") if v], default=[4096, 8192, 32768, 65536],
                     help="comma-separated FP32 sizes of the n sweep (empty: skip)")
     ap.add_argument("--no-sweep", dest="sweep", action="store_const", const=[])
+    ap.add_argument("--sweep-f64", type=lambda x: [int(v) for v in x.split(",") if v], default=[4096, 8192],
+                    help="comma-separated FP64 sizes of the n sweep beside the n=32768 FP64 line (empty: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -157,9 +157,7 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
       kid[a][c] = -1;
     }
   const int kpn = (mK + 1) / 2;
-#pragma unroll 1
-  for (int kp = 0; kp < kpn; ++kp) {
-    unsigned long long a[TM], b[TM];
+  auto load_pair = [&](int kp, unsigned long long (&a)[TM], unsigned long long (&b)[TM]) {
 #pragma unroll
     for (int rr = 0; rr < TM; rr += 2) {
       const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&sm.As[kp][row_at(rr, ty)]);
@@ -172,6 +170,32 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
       b[cc] = t.x;
       b[cc + 1] = t.y;
     }
+  };
+  int kp0 = 0;
+  if constexpr (EAGER) {
+    // Two k-pairs (four k) per step: the index kept is the first pair of the
+    // last chunk that lowered the accumulator strictly (one compare and one
+    // select per four candidates); the k inside is settled after the loop.
+#pragma unroll 1
+    for (; kp0 + 1 < kpn; kp0 += 2) {
+      unsigned long long a0[TM], b0[TM], a1[TM], b1[TM];
+      load_pair(kp0, a0, b0);
+      load_pair(kp0 + 1, a1, b1);
+#pragma unroll
+      for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < TM; ++cc) {
+          const float m1 = mp32::min3f_pair(acc[rr][cc], a0[rr], b0[cc]);
+          const float m2 = mp32::min3f_pair(m1, a1[rr], b1[cc]);
+          kid[rr][cc] = m2 < acc[rr][cc] ? kp0 : kid[rr][cc];
+          acc[rr][cc] = m2;
+        }
+    }
+  }
+#pragma unroll 1
+  for (int kp = kp0; kp < kpn; ++kp) {  // lazy: every pair; eager: an odd last pair
+    unsigned long long a[TM], b[TM];
+    load_pair(kp, a, b);
 #pragma unroll
     for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
@@ -180,15 +204,25 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
         else mp32::relax2(acc[rr][cc], a[rr], b[cc]);
       }
   }
-  if (EAGER) {  // the k inside each output's last improving pair
+  if (EAGER) {  // the first k inside each output's last improving chunk reaching its value
 #pragma unroll
     for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
       for (int cc = 0; cc < TM; ++cc) {
         const int kp = kid[rr][cc];
         if (kp >= 0) {
+          const float g = acc[rr][cc];
           const float2 c = mp32::sum2(sm.As[kp][row_at(rr, ty)], sm.Bs[kp][col_at(cc, tx)]);
-          kid[rr][cc] = c.x == acc[rr][cc] ? 2 * kp : 2 * kp + 1;
+          int k;
+          if (c.x == g) {
+            k = 2 * kp;
+          } else if (c.y == g || kp + 1 >= kpn) {
+            k = 2 * kp + 1;  // (a pair alone at the end has its value in one of its two k)
+          } else {
+            const float2 c2 = mp32::sum2(sm.As[kp + 1][row_at(rr, ty)], sm.Bs[kp + 1][col_at(cc, tx)]);
+            k = c2.x == g ? 2 * kp + 2 : 2 * kp + 3;
+          }
+          kid[rr][cc] = k;
         }
       }
   }
@@ -314,11 +348,11 @@ __device__ __forceinline__ bool solve_graph128_f32(float *__restrict__ D, int32_
     if (R == 1) break;
     for (int side = 0; side < 2; ++side) {  // row blocks (r, J), then column blocks (I, r)
       const bool is_row = side == 0;
-      lines_load_diag(D, ld, n, r, is_row, sm.lines_M);
+      lines_load_diag(D, ld, n, r, is_row);
       __syncthreads();
       for (int o = 0; o < R; ++o) {
         if (o == r) continue;
-        for (int part = 0; part < k2::PARTS; ++part) lines_part_f32(D, ld, P, n, r, o, is_row, part, pan, sm.lines_M);
+        for (int part = 0; part < k2::PARTS; ++part) lines_part_f32(D, ld, P, n, r, o, is_row, part, pan);
       }
       __syncthreads();
     }
@@ -330,7 +364,7 @@ __device__ __forceinline__ bool solve_graph128_f32(float *__restrict__ D, int32_
         if (J == r) continue;
         for (int hJ = 0; hJ < 2; ++hJ) {
           __syncthreads();  // the previous product's epilogue is done with the shared memory
-          if (!minplus_half_f32<true, false>(D, ld, P, n, I, J, hJ, r, vec_ok, pan, smem_raw)) return false;
+          if (!minplus_half_f32<true, false>(D, ld, P, n, I, J, hJ, r, vec_ok, pan)) return false;
         }
       }
     }

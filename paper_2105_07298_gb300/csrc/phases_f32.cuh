@@ -1,6 +1,10 @@
-// Device code of the FP32 phases 2/3 (lines) and phase 4 (block product),
-// shared by the single-graph kernels (fw_single.cu) and the batched
-// persistent kernel (fw_batched.cu).  Internal header.
+// Device code of the FP32 phases 2/3 (lines) and phase 4 (block product).
+// The line code is shared by the single-graph kernel (fw_single.cu) and the
+// batched persistent kernel (fw_batched.cu); the phase-4 block product here
+// is the batched kernel's copy of the single-graph phase-4 kernel
+// (fw_phase3_minplus_f32 in fw_single.cu), written as a device function so
+// that one CTA can run many of them (the single-graph kernel keeps its own
+// body: as a device function its code measured 5 % slower).  Internal header.
 #pragma once
 #include <stdint.h>
 
@@ -40,11 +44,12 @@ constexpr int T = mp32::T, THREADS = 256, LINES = 4, PARTS = T / (THREADS / 32 *
 constexpr int SMEM = T * MS * 4;
 }  // namespace k2
 
-// Fills M[k][pos] with the diagonal block of round r (transposed for row
-// blocks, +inf outside the matrix).  The caller synchronises before use.
-__device__ __forceinline__ void lines_load_diag(const float *__restrict__ D, int64_t ld, int n, int r, bool is_row,
-                                                float *__restrict__ M) {
+// Fills M[k][pos] (the launch's dynamic shared memory from offset 0) with the
+// diagonal block of round r (transposed for row blocks, +inf outside the
+// matrix).  The caller synchronises before use.
+__device__ __forceinline__ void lines_load_diag(const float *__restrict__ D, int64_t ld, int n, int r, bool is_row) {
   using namespace k2;
+  extern __shared__ __align__(16) float M[];  // [T][MS], the launch's dynamic shared memory
   const int base_r = r * T, m_r = min(T, n - base_r);
   const float INF = inf<float>();
   for (int e = threadIdx.x; e < T * T; e += THREADS) {
@@ -56,11 +61,11 @@ __device__ __forceinline__ void lines_load_diag(const float *__restrict__ D, int
 
 // Lines 32 part .. 32 part + 31 of the row block (r, other) (is_row) or the
 // column block (other, r), with M holding the diagonal block in that block
-// type's layout.
+// type's layout (lines_load_diag).
 __device__ __forceinline__ void lines_part_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n,
-                                               int r, int other, bool is_row, int part, const Panels &pan,
-                                               const float *__restrict__ M) {
+                                               int r, int other, bool is_row, int part, const Panels &pan) {
   using namespace k2;
+  extern __shared__ __align__(16) float M[];  // [T][MS], filled by lines_load_diag
   const int base_r = r * T, m_r = min(T, n - base_r);
   const int base_o = other * T, m_o = min(T, n - base_o);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -192,14 +197,17 @@ __device__ __forceinline__ V ld_panel(const V *p) {
 // launch, so the recovery may read them through the non-coherent path; a
 // caller that wrote them earlier in the same launch passes NC = false.
 // Returns false if a bounded wait for a copy ran out (the block is then left
-// unchanged and the error word is set).
+// unchanged and the error word is set).  Uses the launch's dynamic shared
+// memory from offset 0 (sizeof(k3::Smem) bytes).
 template <bool EAGER, bool NC>
 __device__ __forceinline__ bool minplus_half_f32(float *__restrict__ D, int64_t ld, int32_t *__restrict__ P, int n,
-                                                 int I, int J, int hJ, int r, int vec_ok, const Panels &pan,
-                                                 unsigned char *smem_raw) {
+                                                 int I, int J, int hJ, int r, int vec_ok, const Panels &pan) {
   using namespace k3;
   using mp32::col_at;
   using mp32::row_at;
+  // The launch's dynamic shared memory (declared here, not passed, so that
+  // every access compiles as a shared-memory access).
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
   const int baseI = I * T, baseJ = J * T + hJ * H, baseK = r * T;
   const int mI = min(T, n - baseI), mJ = min(H, n - baseJ), mK = min(T, n - baseK);

@@ -9,7 +9,11 @@ ways:
   * eager per-pair tracking (phase 4 early rounds, batched): a three-input
     min folds the candidates of k-pairs (2p, 2p+1); the pair p of the last
     strict decrease is kept, and inside it the lower k is taken if its
-    candidate equals the final value, else the upper one.
+    candidate equals the final value, else the upper one;
+  * eager per-chunk tracking (FP32 phase 4 early rounds, batched 64-block
+    eager): two k-pairs (four k) are folded per step; the chunk of the last
+    strict decrease is kept, and inside it the first k whose candidate
+    equals the final value is taken.
 FP64 pass 1 tests "x below ru(d)" for a float x and a double d; that equals
 "x below d" (a float below d is below the smallest float >= d).
 """
@@ -47,6 +51,19 @@ def eager_pairs(init, cands):
     if kp < 0:
         return acc, -1
     return acc, 2 * kp if cs[2 * kp] == acc else 2 * kp + 1
+
+
+def eager_chunks(init, cands, chunk=4):
+    cs = list(cands) + [math.inf] * (-len(cands) % chunk)
+    acc, kc = init, -1
+    for c in range(len(cs) // chunk):
+        m = min([acc] + cs[chunk * c:chunk * c + chunk])
+        if m < acc:
+            kc = c
+        acc = m
+    if kc < 0:
+        return acc, -1
+    return acc, next(chunk * kc + q for q in range(chunk) if cs[chunk * kc + q] == acc)
 
 
 def _cases(seed, count):
@@ -99,3 +116,12 @@ def test_float_below_double_equals_float_below_its_upper_float_bound():
             if math.isnan(x) or math.isnan(d):
                 continue
             assert (x < _ru32(d)) == (x < d), (x, d)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_eager_chunks_give_the_sequential_path_entry(seed):
+    """Four-candidate chunks (two k-pairs) with the last strictly decreasing
+    chunk kept: the first k inside it that reaches the final value is the
+    sequential loop's last improvement."""
+    for init, cands in _cases(100 + seed, 3000):
+        assert eager_chunks(init, cands) == sequential(init, cands)
