@@ -76,12 +76,14 @@ constexpr int T = 64;           // block edge
 constexpr int TM = 4;           // 4 x 4 outputs per thread, 256 threads
 constexpr int KP = T / 2;       // k-pairs per block
 constexpr int ST = T + 2;       // row stride of the pair arrays (16-byte rows, fewer conflicts)
+constexpr int CS = T + 8;       // row stride of Cs / Ks: a warp's 8-byte stores (four rows two
+                                // apart) take the minimum two shared-memory wavefronts
 
 struct ProdSmem {
   unsigned long long As[KP][ST];  // As[kp][i] = (A[i][2kp], A[i][2kp+1])
   unsigned long long Bs[KP][ST];  // Bs[kp][j] = (B[2kp][j], B[2kp+1][j])
-  float Cs[T][T];                 // new candidates
-  int Ks[T][T];                   // eager variant: first argmin k
+  float Cs[T][CS];                // new candidates
+  int Ks[T][CS];                  // eager variant: first argmin k
 };
 }  // namespace b64
 
