@@ -417,3 +417,17 @@ def test_dpx_add_min_rate_is_measured():
     r_dpx = apsp.measure_peak(-4)
     r32 = apsp.measure_peak(4)
     assert 8.0 < r_dpx <= 132.0 and r32 > 0
+
+
+def test_int32_leading_dimension_and_no_path():
+    """int32 with ld > n (padding columns untouched) and without a path matrix."""
+    n, ld = 130, 133
+    W = graphgen.dense_graph(n, 0.3, 55, dtype=np.float64)
+    Wi = np.where(np.isfinite(W), W, apsp.I32_INF).astype(np.int32)
+    buf = torch.full((n, ld), -5, dtype=torch.int32, device=DEV)
+    buf[:, :n] = torch.from_numpy(Wi).to(DEV)
+    apsp.apsp_fw_i32(buf[:, :n])
+    Dh = buf[:, :n].cpu().numpy().astype(np.int64)
+    ref = oracle.fw(W)[0]
+    np.testing.assert_array_equal(Dh, np.where(np.isfinite(ref), ref, apsp.I32_INF).astype(np.int64))
+    assert (buf[:, n:] == -5).all()

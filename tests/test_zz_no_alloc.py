@@ -33,6 +33,8 @@ class _DriverMemory:
     """Device memory counters read through the CUDA driver API (libcuda)."""
 
     def __init__(self):
+        torch.zeros(1, device=DEV)  # the runtime's primary context is current on this thread
+        torch.cuda.synchronize()
         self.cu = ctypes.CDLL("libcuda.so.1")
         self.pool = ctypes.c_void_p()
         dev = ctypes.c_int()
