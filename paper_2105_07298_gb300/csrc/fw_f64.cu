@@ -526,7 +526,9 @@ __global__ void __launch_bounds__(THREADS, EAGER ? 2 : 3)
     }
     const unsigned long long(*As)[KP][H] = sm.Alo[st];
     const unsigned long long(*Bs)[H] = sm.Blo[st];
-#pragma unroll 1
+// Unrolled by four: the shared loads of later k-pairs are scheduled ahead of
+    // the current one's arithmetic (measured best of 1, 2, 4, 8 and 16).
+#pragma unroll 4
     for (int kp = 0; kp < KP; ++kp) {
       unsigned long long a[4], b[8];
 #pragma unroll
