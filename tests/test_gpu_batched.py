@@ -210,3 +210,24 @@ def test_variant_table_names_block_and_tile():
     assert info[0] == {"block": 64, "tile": "4x4", "path": "lazy"}
     assert info[1] == {"block": 64, "tile": "4x4", "path": "eager"}
     assert info[2] == {"block": 128, "tile": "8x4", "path": "eager"}
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_one_shot_and_no_path_for_every_variant(variant):
+    """The one-shot entry point (its work list and, for the 128-block variant,
+    the per-CTA panels in one stream-ordered allocation) and runs without a
+    path matrix, for every variant: distances exact on integer weights."""
+    saved = [B.get_variant(c) for c in range(B.num_classes())]
+    try:
+        for c in range(B.num_classes()):
+            B.set_variant(c, variant)
+        sizes = [3, 64, 129, 300, 511, 700]
+        mats = [graphgen.dense_graph(n, 0.3, 2200 + n) for n in sizes]
+        for W, (D, P) in zip(mats, _solve(sizes, mats, plan=False)):
+            np.testing.assert_array_equal(D, oracle.fw(W)[0])
+            assert oracle.check_paths(W, D, P) == 0
+        for W, (D, _) in zip(mats, _solve(sizes, mats, with_path=False)):
+            np.testing.assert_array_equal(D, oracle.fw(W)[0])
+    finally:
+        for c, v in enumerate(saved):
+            B.set_variant(c, v)
