@@ -20,7 +20,10 @@
 //                 in shared memory (k-pair layout);
 //     path matrix: variant 0 recovers each improved output's first argmin k
 //     from the operands after the product (lazy), variant 1 keeps the index
-//     of the last improving k-pair in the inner loop (eager).
+//     of the last improving k-pair in the inner loop (eager);
+//     variant 1, and every variant run without a path matrix, pipelines the
+//     products of a phase group: the operands of the next product are copied
+//     into a second shared-memory stage while the current one computes.
 //   variant 2, 128 x 128 blocks, 8 x 4 register tile per thread: the
 //     single-graph kernels' code run by one CTA: the register-resident closure
 //     for phase 1, the k-sequential line kernel for phases 2+3 (the paper's
@@ -85,10 +88,16 @@ struct ProdSmem {
   float Cs[T][CS];                // new candidates
   int Ks[T][CS];                  // eager variant: first argmin k
 };
+// Operand stage of the pipelined products: the same k-pair layout.
+struct Stage {
+  unsigned long long As[KP][ST];
+  unsigned long long Bs[KP][ST];
+};
 }  // namespace b64
 
 union BatchedSmem {
   b64::ProdSmem prod;
+  b64::Stage stage[2];
   mp32::DiagSmemT<64> diag;
   mp32::DiagSmemT<128> diag128;
   float lines_M[k2::T * k2::MS];
@@ -330,6 +339,205 @@ __device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *
   __syncthreads();
 }
 
+// --------------------------------------------------------------------------
+// Pipelined 64-block products (variant 1, and every variant without a path
+// matrix).  The products of one group (phases 2+3 of a round, or its phase 4)
+// neither read nor write a block another product of the group writes, so the
+// operands of product p+1 are copied into the second stage while product p
+// computes.  The accumulator starts at C itself, so an output's pair index is
+// set only when a candidate beats C strictly, which is the sequential loop's
+// rule, and only such outputs are resolved and written (from registers).
+// --------------------------------------------------------------------------
+
+// Both operand blocks of one product into a stage (4-byte asynchronous
+// copies into the k-pair layout, +inf outside the valid extents), committed
+// as one group.
+__device__ __forceinline__ void stage_operands(b64::Stage &s, const float *__restrict__ D, int ld, int baseI,
+                                               int baseJ, int baseK, int mI, int mJ, int mK) {
+  using namespace b64;
+  const int tid = threadIdx.x;
+  const float INF = inf<float>();
+  float *as = reinterpret_cast<float *>(&s.As[0][0]);
+  float *bs = reinterpret_cast<float *>(&s.Bs[0][0]);
+#pragma unroll
+  for (int q = 0; q < T * T / 256; ++q) {
+    const int idx = tid + q * 256, i = idx / T, k = idx % T;
+    float *dst = as + ((k >> 1) * ST + i) * 2 + (k & 1);
+    if (i < mI && k < mK) mp32::cp_async4(dst, D + (int64_t)(baseI + i) * ld + baseK + k);
+    else *dst = INF;
+  }
+#pragma unroll
+  for (int q = 0; q < T * T / 256; ++q) {
+    const int idx = tid + q * 256, k = idx / T, j = idx % T;
+    float *dst = bs + ((k >> 1) * ST + j) * 2 + (k & 1);
+    if (j < mJ && k < mK) mp32::cp_async4(dst, D + (int64_t)(baseK + k) * ld + baseJ + j);
+    else *dst = INF;
+  }
+  mp32::cp_async_commit();
+}
+
+// C(baseI, baseJ) <- min(C, A (x) B) from a filled stage, TB = 64, all 256
+// threads; TRACK writes P (the first k whose candidate beats C strictly).
+template <bool TRACK>
+__device__ __forceinline__ void product64_staged(float *__restrict__ D, int ld, int32_t *__restrict__ P, int baseI,
+                                                 int baseJ, int baseK, int mI, int mJ, int mK,
+                                                 const b64::Stage &s) {
+  using namespace b64;
+  using mp32::col_at;
+  using mp32::row_at;
+  const int ty = mp32::thread_ty(), tx = mp32::thread_tx();
+  const float INF = inf<float>();
+  float acc[TM][TM];
+  // TRACK: the first pair of the last chunk that lowered the accumulator
+  // (-1: none); otherwise C itself, to find the improved outputs.
+  int aux[TM][TM];
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < TM; ++cc) {
+      const int i = row_at(rr, ty), j = col_at(cc, tx);
+      acc[rr][cc] = (i < mI && j < mJ) ? D[(int64_t)(baseI + i) * ld + baseJ + j] : INF;
+      aux[rr][cc] = TRACK ? -1 : __float_as_int(acc[rr][cc]);
+    }
+  const int kpn = (mK + 1) / 2;
+  auto load_pair = [&](int kp, unsigned long long (&a)[TM], unsigned long long (&b)[TM]) {
+#pragma unroll
+    for (int rr = 0; rr < TM; rr += 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&s.As[kp][row_at(rr, ty)]);
+      a[rr] = t.x;
+      a[rr + 1] = t.y;
+    }
+#pragma unroll
+    for (int cc = 0; cc < TM; cc += 2) {
+      const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(&s.Bs[kp][col_at(cc, tx)]);
+      b[cc] = t.x;
+      b[cc + 1] = t.y;
+    }
+  };
+  int kp0 = 0;
+  if constexpr (TRACK) {
+    // Two k-pairs (four k) per step, one compare and one select per output.
+#pragma unroll 1
+    for (; kp0 + 1 < kpn; kp0 += 2) {
+      unsigned long long a0[TM], b0[TM], a1[TM], b1[TM];
+      load_pair(kp0, a0, b0);
+      load_pair(kp0 + 1, a1, b1);
+#pragma unroll
+      for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < TM; ++cc) {
+          const float m1 = mp32::min3f_pair(acc[rr][cc], a0[rr], b0[cc]);
+          const float m2 = mp32::min3f_pair(m1, a1[rr], b1[cc]);
+          aux[rr][cc] = m2 < acc[rr][cc] ? kp0 : aux[rr][cc];
+          acc[rr][cc] = m2;
+        }
+    }
+  }
+#pragma unroll 1
+  for (int kp = kp0; kp < kpn; ++kp) {  // TRACK: an odd last pair only
+    unsigned long long a[TM], b[TM];
+    load_pair(kp, a, b);
+#pragma unroll
+    for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < TM; ++cc) {
+        if (TRACK) relax2_argpair(acc[rr][cc], aux[rr][cc], a[rr], b[cc], kp);
+        else mp32::relax2(acc[rr][cc], a[rr], b[cc]);
+      }
+  }
+#pragma unroll
+  for (int rr = 0; rr < TM; ++rr)
+#pragma unroll
+    for (int cc = 0; cc < TM; ++cc) {
+      const int i = row_at(rr, ty), j = col_at(cc, tx);
+      const float g = acc[rr][cc];
+      const int64_t e = (int64_t)(baseI + i) * ld + baseJ + j;
+      if constexpr (TRACK) {
+        const int kp = aux[rr][cc];
+        if (kp >= 0) {  // improved: the first k of the chunk whose candidate is the final value
+          const float2 c = mp32::sum2(s.As[kp][i], s.Bs[kp][j]);
+          int k;
+          if (c.x == g) {
+            k = 2 * kp;
+          } else if (c.y == g || kp + 1 >= kpn) {
+            k = 2 * kp + 1;
+          } else {
+            const float2 c2 = mp32::sum2(s.As[kp + 1][i], s.Bs[kp + 1][j]);
+            k = c2.x == g ? 2 * kp + 2 : 2 * kp + 3;
+          }
+          D[e] = g;
+          P[e] = baseK + k;
+        }
+      } else {
+        if (g < __int_as_float(aux[rr][cc])) D[e] = g;
+      }
+    }
+}
+
+// The products of round r (base = 64 r, m valid vertices) in group 0 (phases
+// 2+3: the row blocks (r, J), then the column blocks (I, r), each a product
+// with the closed diagonal block) or group 1 (phase 4), two stages deep.
+template <bool TRACK>
+__device__ __forceinline__ void run_group64(float *__restrict__ D, int ld, int32_t *__restrict__ P, int n, int r,
+                                            int group, b64::Stage (&st)[2]) {
+  constexpr int T = b64::T;
+  const int R = (n + T - 1) / T, base = r * T, m = min(T, n - base);
+  const int np = group == 0 ? 2 * (R - 1) : (R - 1) * (R - 1);
+  auto coords = [&](int p, int &bI, int &bJ, int &mI, int &mJ) {
+    int I, J;
+    if (group == 0) {
+      const int o = p % (R - 1), O = o < r ? o : o + 1;
+      I = p < R - 1 ? r : O;
+      J = p < R - 1 ? O : r;
+    } else {
+      const int a = p / (R - 1), b = p % (R - 1);
+      I = a < r ? a : a + 1;
+      J = b < r ? b : b + 1;
+    }
+    bI = I * T;
+    bJ = J * T;
+    mI = min(T, n - bI);
+    mJ = min(T, n - bJ);
+  };
+  int bI, bJ, mI, mJ;
+  coords(0, bI, bJ, mI, mJ);
+  stage_operands(st[0], D, ld, bI, bJ, base, mI, mJ, m);
+#pragma unroll 1
+  for (int p = 0; p < np; ++p) {
+    int cI, cJ, cmI, cmJ;
+    coords(p, cI, cJ, cmI, cmJ);
+    if (p + 1 < np) {
+      __syncthreads();  // product p-1 is done with the stage refilled here
+      coords(p + 1, bI, bJ, mI, mJ);
+      stage_operands(st[(p + 1) & 1], D, ld, bI, bJ, base, mI, mJ, m);
+      mp32::cp_async_wait<1>();
+    } else {
+      mp32::cp_async_wait<0>();
+    }
+    __syncthreads();  // every thread's copies into stage p & 1 are visible
+    product64_staged<TRACK>(D, ld, P, cI, cJ, base, cmI, cmJ, m, st[p & 1]);
+  }
+}
+
+template <bool TRACK>
+__device__ __forceinline__ void solve_graph_pipe_f32(float *__restrict__ D, int32_t *__restrict__ P, int n,
+                                                     BatchedSmem &sm) {
+  constexpr int T = b64::T;
+  const int ld = n;
+  const int R = (n + T - 1) / T;
+  for (int r = 0; r < R; ++r) {
+    const int base = r * T, m = min(T, n - base);
+    __syncthreads();  // the previous round's products are done with the stages
+    mp32::diag_closure<4>(D, ld, P, base, m, sm.diag);
+    __syncthreads();
+    if (R == 1) break;
+    run_group64<TRACK>(D, ld, P, n, r, 0, sm.stage);
+    __syncthreads();  // the panels are final (and visible) before phase 4 copies them
+    run_group64<TRACK>(D, ld, P, n, r, 1, sm.stage);
+  }
+  __syncthreads();
+}
+
 // The 128-block variant: the single-graph phases run by this CTA alone.
 // The panels (this CTA's scratch) are rewritten every round, so the product's
 // path recovery reads them through the coherent path (NC = false), and every
@@ -421,8 +629,10 @@ __device__ __forceinline__ void persistent_body(float *__restrict__ Dp, int32_t 
         continue;
       }
     }
-    if (variant == 1 || variant == 2)
-      solve_graph_f32<true>(D, P, n, sm);
+    if (!P)
+      solve_graph_pipe_f32<false>(D, P, n, sm);
+    else if (variant == 1 || variant == 2)
+      solve_graph_pipe_f32<true>(D, P, n, sm);
     else
       solve_graph_f32<false>(D, P, n, sm);
   }
