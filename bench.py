@@ -334,27 +334,26 @@ def bench_e2e(torch, apsp, graphgen, W_dev, args):
     P = torch.empty((n, n), dtype=torch.int32, device=W_dev.device)
 
     reps = max(1, min(args.steps, 2))
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps + 1)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(reps + 1)]
     it = iter(range(reps + 1))
 
     def step():
         e = ev[next(it)]
-        D.copy_(Wh, non_blocking=True)
         e[0].record()
-        apsp.apsp_fw_f32(D, P)
+        D.copy_(Wh, non_blocking=True)
         e[1].record()
+        apsp.apsp_fw_f32(D, P)
+        e[2].record()
         Dh.copy_(D, non_blocking=True)
         Ph.copy_(P, non_blocking=True)
-        e[2].record()
+        e[3].record()
 
     step()
     torch.cuda.synchronize()
     t = time_events(torch, step, reps)
-    # parts of the timed steps: the solve, and the copies around it
-    solve = sum(e[0].elapsed_time(e[1]) for e in ev[1:]) / reps
-    d2h = sum(e[1].elapsed_time(e[2]) for e in ev[1:]) / reps
-    parts = {"step_ms": 1e3 * t / reps, "solve_ms": solve, "d2h_ms": d2h,
-             "h2d_ms": 1e3 * t / reps - solve - d2h}
+    # parts of the timed steps: the copies and the solve between them
+    part = [sum(e[q].elapsed_time(e[q + 1]) for e in ev[1:]) / reps for q in range(3)]
+    parts = {"step_ms": 1e3 * t / reps, "h2d_ms": part[0], "solve_ms": part[1], "d2h_ms": part[2]}
     return n ** 3 / (t / reps), n * n * 4, n * n * 8, Wh, parts
 
 
