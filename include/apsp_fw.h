@@ -97,6 +97,31 @@ int apsp_fw_block_size(int elem_bytes);
 int apsp_fw_f32(float *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
 int apsp_fw_f64(double *d_dist, int64_t n, int64_t ld, int32_t *d_path, void *stream);
 
+/* ------------------------------------------------------------------------
+ * The same FP32 solve from and to HOST memory (the end-to-end call): copies
+ * the weights to the device, runs apsp_fw_f32 there, copies D (and P) back,
+ * and returns when the results are in host memory.
+ *
+ *   h_weights   : n x n row-major edge weights (ld = n), HOST, read only.
+ *   h_dist      : n x n row-major output distances, HOST (may be h_weights).
+ *   h_path      : optional n x n int32 output path matrix, HOST, or NULL.
+ *   n           : 0 <= n <= 262144 (n = 0 is a no-op).
+ *   d_work_dist : optional DEVICE buffer of n*n floats that the call uses as
+ *                 D (a caller that solves repeatedly keeps it); NULL: one is
+ *                 allocated stream-ordered on `stream` and freed before return.
+ *   d_work_path : the same for P (n*n int32; used only if h_path != NULL).
+ *   stream      : cudaStream_t as void*; work is ordered after earlier work on
+ *                 it, and the call synchronizes it before returning.
+ * Host buffers page-locked by cudaHostAlloc / cudaHostRegister copy at the
+ * link's rate; pageable ones work too (the driver stages them).  The caller
+ * owns every buffer.  Returns APSP_OK, APSP_EINVAL (n out of range, NULL
+ * h_weights or h_dist with n > 0), APSP_ENOMEM (a work buffer), APSP_ECUDA,
+ * or APSP_ETIMEOUT / APSP_EUNSUPPORTED as apsp_device_status reports them
+ * (the call reads and clears those device error words).
+ * ---------------------------------------------------------------------- */
+int apsp_fw_f32_host(const float *h_weights, float *h_dist, int32_t *h_path, int64_t n,
+                     float *d_work_dist, int32_t *d_work_path, void *stream);
+
 /* Integer weights (int32), exact.  Same conventions with APSP_I32_INF
  * (INT32_MAX) in place of +infinity (no edge, no path).  Every int32 weight
  * is allowed (negative ones without a negative cycle).  The solve runs on the

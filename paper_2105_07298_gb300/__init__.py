@@ -46,6 +46,7 @@ SIGNATURES = {
     "apsp_fw_backward_f32": (ctypes.c_int, [_p, _p, _p, _p, _i64, _i64, _i64, _i64, _p, _p]),
     "apsp_fw_backward_packed_f32": (ctypes.c_int, [_p, _p, _p, _p, _p, _p, _i32, _p, _p]),
     "apsp_check_negative_cycle": (ctypes.c_int, [_p, ctypes.c_int, _i64, _i64, _p]),
+    "apsp_fw_f32_host": (ctypes.c_int, [_p, _p, _p, _i64, _p, _p, _p]),
     "apsp_wait_timeout_selftest": (ctypes.c_int, [ctypes.c_uint32, _p]),
     "apsp_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "apsp_device_status": (ctypes.c_int, [_p]),
@@ -134,6 +135,50 @@ def apsp_fw_f32(dist, path=None, stream=None):
     """In-place FP32 blocked Floyd-Warshall on a CUDA n x n tensor (optionally writing ``path``)."""
     import torch
     return _fw("apsp_fw_f32", dist, path, stream, torch.float32)
+
+
+def _host_matrix(t, dtype, n=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("expected a CPU (host) tensor")
+    if t.dtype != dtype or t.dim() != 2 or t.shape[0] != t.shape[1] or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous n x n {dtype} host matrix")
+    if n is not None and t.shape[0] != n:
+        raise ValueError("host matrices must have the same n")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _device_work(t, dtype, n):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or t.numel() < n * n \
+            or not t.is_contiguous():
+        raise ValueError(f"work buffer must be a contiguous CUDA {dtype} tensor of at least n*n elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def apsp_fw_f32_host(weights, dist=None, path=None, work_dist=None, work_path=None, stream=None,
+                     with_path=True):
+    """FP32 solve from and to host memory (the end-to-end call, one C-ABI call):
+    ``weights`` is a contiguous CPU float32 n x n tensor; the distances go to
+    ``dist`` and the path matrix to ``path`` (CPU tensors; page-locked ones are
+    allocated when None; ``with_path=False`` skips P).  ``work_dist`` /
+    ``work_path``: optional CUDA tensors the call uses on the device (kept by a
+    caller that solves repeatedly).  Returns (dist, path)."""
+    import torch
+    wp = _host_matrix(weights, torch.float32)
+    n = weights.shape[0]
+    if dist is None:
+        dist = torch.empty((n, n), dtype=torch.float32, pin_memory=torch.cuda.is_available())
+    if with_path and path is None:
+        path = torch.empty((n, n), dtype=torch.int32, pin_memory=torch.cuda.is_available())
+    dp = _host_matrix(dist, torch.float32, n)
+    pp = _host_matrix(path, torch.int32, n) if with_path else None
+    st = load().apsp_fw_f32_host(wp, dp, pp, n, _device_work(work_dist, torch.float32, n),
+                                 _device_work(work_path, torch.int32, n), _stream_ptr(stream))
+    _check(st, "apsp_fw_f32_host")
+    return dist, (path if with_path else None)
 
 
 def apsp_fw_f64(dist, path=None, stream=None):

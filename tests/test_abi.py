@@ -75,6 +75,10 @@ def test_new_entry_points_reject_bad_arguments_without_gpu():
     assert L.apsp_wait_timeout_selftest(0, None) == apsp.APSP_EINVAL
     assert L.apsp_wait_timeout_selftest((1 << 22) + 1, None) == apsp.APSP_EINVAL
     assert L.apsp_fw_backward_packed_f32(None, None, None, None, None, None, -1, None, None) == apsp.APSP_EINVAL
+    assert L.apsp_fw_f32_host(None, None, None, 0, None, None, None) == apsp.APSP_OK  # n = 0: no-op
+    assert L.apsp_fw_f32_host(None, None, None, 5, None, None, None) == apsp.APSP_EINVAL
+    assert L.apsp_fw_f32_host(None, None, None, -1, None, None, None) == apsp.APSP_EINVAL
+    assert L.apsp_fw_f32_host(None, None, None, (1 << 18) + 1, None, None, None) == apsp.APSP_EINVAL
     for st in range(8):
         assert L.apsp_status_string(st).startswith(b"APSP_")
     assert L.apsp_status_string(7) == b"APSP_ETIMEOUT: a kernel's bounded wait for an asynchronous copy ran out"

@@ -152,6 +152,41 @@ def test_without_path_matrix(dtype):
     np.testing.assert_array_equal(D.astype(np.float64), oracle.fw(W.astype(np.float64))[0])
 
 
+def test_host_buffer_entry_matches_device_path():
+    """apsp_fw_f32_host (host buffers in and out, one C-ABI call) gives the
+    device entry point's D and P bit for bit, from page-locked and pageable
+    buffers, with and without caller work buffers, with and without P, in
+    place; integer weights also against the oracle."""
+    n = 700
+    W = graphgen.dense_graph(n, 0.3, 77, weights="real", lo=0.5, hi=2.0)
+    Dd = torch.from_numpy(W.copy()).to(DEV)
+    Pd = torch.empty((n, n), dtype=torch.int32, device=DEV)
+    apsp.apsp_fw_f32(Dd, Pd)
+    torch.cuda.synchronize()
+    Dref, Pref = Dd.cpu(), Pd.cpu()
+    for pinned in (True, False):
+        Wh = torch.from_numpy(W.copy())
+        if pinned:
+            Wh = Wh.pin_memory()
+        for work in (False, True):
+            wd = torch.empty(n * n, device=DEV) if work else None
+            wp = torch.empty(n * n, dtype=torch.int32, device=DEV) if work else None
+            D, P = apsp.apsp_fw_f32_host(Wh, work_dist=wd, work_path=wp)
+            assert torch.equal(D, Dref) and torch.equal(P, Pref)
+            assert torch.equal(Wh, torch.from_numpy(W))  # the input is read only
+    D, P = apsp.apsp_fw_f32_host(torch.from_numpy(W.copy()), with_path=False)
+    assert P is None and torch.equal(D, Dref)
+    Wi = torch.from_numpy(W.copy())
+    apsp.apsp_fw_f32_host(Wi, dist=Wi, with_path=False)
+    assert torch.equal(Wi, Dref)
+    Wint = graphgen.dense_graph(300, 0.3, 78)
+    D, P = apsp.apsp_fw_f32_host(torch.from_numpy(Wint.copy()))
+    np.testing.assert_array_equal(D.numpy(), oracle.fw(Wint)[0])
+    assert oracle.check_paths(Wint, D.numpy(), P.numpy()) == 0
+    with pytest.raises(TypeError):
+        apsp.apsp_fw_f32_host(Dd)  # device tensors go to apsp_fw_f32
+
+
 def test_structured_graphs():
     # chain across several blocks, grid, disconnected halves, negative weights via potentials
     W = graphgen.chain_graph(np.arange(1, 300, dtype=np.float64) % 7 + 1).astype(np.float32)
