@@ -419,6 +419,14 @@ def bench_batched(torch, apsp, graphgen, args, dev):
     torch.cuda.synchronize()
     D.copy_(W)
     t_pg = time_events(torch, per_graph, 1)
+    # the same plan without a path matrix (distances only), plain launches
+    def step_np():
+        D.copy_(W)
+        plan.run(D)
+
+    step_np()
+    torch.cuda.synchronize()
+    t_np = max(time_events(torch, step_np, reps) / reps - t_copy, 1e-9)
     relax = float(np.sum(sizes.astype(np.float64) ** 3))
     plan.close()
     facts = device_facts(torch)
@@ -427,6 +435,8 @@ def bench_batched(torch, apsp, graphgen, args, dev):
             "graphs_per_s": 4096 / t_solve, "ms": 1e3 * t_solve, "relax_per_s": relax / t_solve,
             "frac_of_unit_peak": relax / t_solve / peak,
             "per_graph_launches": {"graphs_per_s": 4096 / t_pg, "ms": 1e3 * t_pg},
+            "without_path": {"ms": 1e3 * t_np, "relax_per_s": relax / t_np,
+                             "frac_of_unit_peak": relax / t_np / peak},
             "speedup_vs_per_graph": t_pg / t_solve,
             "autotuned_variants": {str(c): {"variant": r["variant"], "bounds": r["bounds"], "shape": r["shape"],
                                             "ms_per_variant": r["ms"]} for c, r in tuned.items()},
@@ -791,7 +801,8 @@ def summary_of(details, line):
     if b:
         out["batched"] = {"graphs_per_s": round(b["graphs_per_s"]), "ms": round(b["ms"], 3),
                           "relax_per_s": float("%.4g" % b["relax_per_s"]), "frac": round(b["frac_of_unit_peak"], 4),
-                          "vs_per_graph": round(b["speedup_vs_per_graph"], 1)}
+                          "vs_per_graph": round(b["speedup_vs_per_graph"], 1),
+                          "no_path_ms": round(b["without_path"]["ms"], 3)}
     bs = details.get("batched_sharded")
     if bs:
         out["batched_sharded"] = {"graphs_per_s": round(bs["graphs_per_s"]), "ranks": bs["ranks"]}
