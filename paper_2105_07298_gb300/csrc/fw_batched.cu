@@ -7,8 +7,8 @@
 // CTA ever waits on another.
 //
 // Per graph (n_g <= 1024, row-major, ld = n_g) the CTA runs the blocked FW of
-// §2.2 on the matrix in global memory (it stays in L2), with one of four
-// kernel variants chosen per size class by the autotuner:
+// §2.2 on the matrix in global memory, with one of three kernel variants
+// chosen per size class by the autotuner:
 //   variants 0 and 1, 64 x 64 blocks, 4 x 4 register tile per thread:
 //     phase 1     register-resident closure of the diagonal block;
 //     phases 2+3  row block (r,J) <- min(C, D*(r,r) (x) C) and column block
@@ -79,14 +79,13 @@ constexpr int T = 64;           // block edge
 constexpr int TM = 4;           // 4 x 4 outputs per thread, 256 threads
 constexpr int KP = T / 2;       // k-pairs per block
 constexpr int ST = T + 2;       // row stride of the pair arrays (16-byte rows, fewer conflicts)
-constexpr int CS = T + 8;       // row stride of Cs / Ks: a warp's 8-byte stores (four rows two
+constexpr int CS = T + 8;       // row stride of Cs: a warp's 8-byte stores (four rows two
                                 // apart) take the minimum two shared-memory wavefronts
 
 struct ProdSmem {
   unsigned long long As[KP][ST];  // As[kp][i] = (A[i][2kp], A[i][2kp+1])
   unsigned long long Bs[KP][ST];  // Bs[kp][j] = (B[2kp][j], B[2kp+1][j])
   float Cs[T][CS];                // new candidates
-  int Ks[T][CS];                  // eager variant: first argmin k
 };
 // Operand stage of the pipelined products: the same k-pair layout.
 struct Stage {
@@ -130,12 +129,13 @@ __device__ __forceinline__ void relax2_argpair(float &acc, int &kp_last, unsigne
 }
 
 // C(baseI, baseJ) <- min(C, A(baseI, baseK) (x) B(baseK, baseJ)), TB = 64,
-// all 256 threads.  C may be the same block as A or B: the operands are
-// copied to shared memory first and C is written only after every read.
-template <bool EAGER>
-__device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t *__restrict__ P,
-                                          int baseI, int baseJ, int baseK, int mI, int mJ, int mK,
-                                          b64::ProdSmem &sm) {
+// all 256 threads, the lazy path matrix of variant 0 (each improved output's
+// first argmin k recovered from the operands after the product).  C may be
+// the same block as A or B: the operands are copied to shared memory first
+// and C is written only after every read.
+__device__ __forceinline__ void product64_lazy(float *__restrict__ D, int ld, int32_t *__restrict__ P,
+                                               int baseI, int baseJ, int baseK, int mI, int mJ, int mK,
+                                               b64::ProdSmem &sm) {
   using namespace b64;
   using mp32::col_at;
   using mp32::row_at;
@@ -165,14 +165,10 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
   }
   __syncthreads();
   float acc[TM][TM];
-  int kid[TM][TM];
 #pragma unroll
   for (int a = 0; a < TM; ++a)
 #pragma unroll
-    for (int c = 0; c < TM; ++c) {
-      acc[a][c] = INF;
-      kid[a][c] = -1;
-    }
+    for (int c = 0; c < TM; ++c) acc[a][c] = INF;
   const int kpn = (mK + 1) / 2;
   auto load_pair = [&](int kp, unsigned long long (&a)[TM], unsigned long long (&b)[TM]) {
 #pragma unroll
@@ -188,72 +184,23 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
       b[cc + 1] = t.y;
     }
   };
-  int kp0 = 0;
-  if constexpr (EAGER) {
-    // Two k-pairs (four k) per step: the index kept is the first pair of the
-    // last chunk that lowered the accumulator strictly (one compare and one
-    // select per four candidates); the k inside is settled after the loop.
 #pragma unroll 1
-    for (; kp0 + 1 < kpn; kp0 += 2) {
-      unsigned long long a0[TM], b0[TM], a1[TM], b1[TM];
-      load_pair(kp0, a0, b0);
-      load_pair(kp0 + 1, a1, b1);
-#pragma unroll
-      for (int rr = 0; rr < TM; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < TM; ++cc) {
-          const float m1 = mp32::min3f_pair(acc[rr][cc], a0[rr], b0[cc]);
-          const float m2 = mp32::min3f_pair(m1, a1[rr], b1[cc]);
-          kid[rr][cc] = m2 < acc[rr][cc] ? kp0 : kid[rr][cc];
-          acc[rr][cc] = m2;
-        }
-    }
-  }
-#pragma unroll 1
-  for (int kp = kp0; kp < kpn; ++kp) {  // lazy: every pair; eager: an odd last pair
+  for (int kp = 0; kp < kpn; ++kp) {
     unsigned long long a[TM], b[TM];
     load_pair(kp, a, b);
 #pragma unroll
     for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
-      for (int cc = 0; cc < TM; ++cc) {
-        if (EAGER) relax2_argpair(acc[rr][cc], kid[rr][cc], a[rr], b[cc], kp);
-        else mp32::relax2(acc[rr][cc], a[rr], b[cc]);
-      }
+      for (int cc = 0; cc < TM; ++cc) mp32::relax2(acc[rr][cc], a[rr], b[cc]);
   }
-  if (EAGER) {  // the first k inside each output's last improving chunk reaching its value
-#pragma unroll
-    for (int rr = 0; rr < TM; ++rr)
-#pragma unroll
-      for (int cc = 0; cc < TM; ++cc) {
-        const int kp = kid[rr][cc];
-        if (kp >= 0) {
-          const float g = acc[rr][cc];
-          const float2 c = mp32::sum2(sm.As[kp][row_at(rr, ty)], sm.Bs[kp][col_at(cc, tx)]);
-          int k;
-          if (c.x == g) {
-            k = 2 * kp;
-          } else if (c.y == g || kp + 1 >= kpn) {
-            k = 2 * kp + 1;  // (a pair alone at the end has its value in one of its two k)
-          } else {
-            const float2 c2 = mp32::sum2(sm.As[kp + 1][row_at(rr, ty)], sm.Bs[kp + 1][col_at(cc, tx)]);
-            k = c2.x == g ? 2 * kp + 2 : 2 * kp + 3;
-          }
-          kid[rr][cc] = k;
-        }
-      }
-  }
-  // Epilogue: candidates (and eager argmins) to shared memory; each warp
-  // then owns 8 whole rows, lane l the columns 2l and 2l+1.
+  // Epilogue: candidates to shared memory; each warp then owns 8 whole rows,
+  // lane l the columns 2l and 2l+1.
 #pragma unroll
   for (int rr = 0; rr < TM; ++rr)
 #pragma unroll
     for (int cc = 0; cc < TM; cc += 2) {
       *reinterpret_cast<float2 *>(&sm.Cs[row_at(rr, ty)][col_at(cc, tx)]) =
           make_float2(acc[rr][cc], acc[rr][cc + 1]);
-      if (EAGER)
-        *reinterpret_cast<int2 *>(&sm.Ks[row_at(rr, ty)][col_at(cc, tx)]) =
-            make_int2(kid[rr][cc], kid[rr][cc + 1]);
     }
   __syncthreads();
   const int i0 = w * 8, j0 = 2 * lane;
@@ -269,7 +216,7 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
 #pragma unroll
     for (int q = 0; q < 2; ++q)
       if (sm.Cs[i0 + t][j0 + q] < o[t][q]) flags |= 1u << (2 * t + q);
-  if (P && !EAGER) {
+  if (P) {
     // lazy P: one improved output per warp pass; lane l tests k = 2l, 2l+1
     // with one paired add of As[l][i] and Bs[l][j] (shared memory).
     unsigned wflags = __reduce_or_sync(kFullMask, flags);
@@ -310,12 +257,11 @@ __device__ __forceinline__ void product64(float *__restrict__ D, int ld, int32_t
       if ((flags >> (2 * t + q)) & 1u) {
         const int64_t g = (int64_t)(baseI + i0 + t) * ld + baseJ + j0 + q;
         D[g] = sm.Cs[i0 + t][j0 + q];
-        if (EAGER && P) P[g] = baseK + sm.Ks[i0 + t][j0 + q];
       }
 }
 
-template <bool EAGER>
-__device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *__restrict__ P,
+// Variant 0 with a path matrix: unpipelined products, lazy path recovery.
+__device__ __forceinline__ void solve_graph_lazy_f32(float *__restrict__ D, int32_t *__restrict__ P,
                                                 int n, BatchedSmem &sm) {
   constexpr int T = b64::T;
   const int ld = n;
@@ -327,18 +273,18 @@ __device__ __forceinline__ void solve_graph_f32(float *__restrict__ D, int32_t *
     __syncthreads();
     for (int J = 0; J < R; ++J) {
       if (J == r) continue;
-      product64<EAGER>(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, sm.prod);
+      product64_lazy(D, ld, P, base, J * T, base, m, min(T, n - J * T), m, sm.prod);
     }
     for (int I = 0; I < R; ++I) {
       if (I == r) continue;
-      product64<EAGER>(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, sm.prod);
+      product64_lazy(D, ld, P, I * T, base, base, min(T, n - I * T), m, m, sm.prod);
     }
     __syncthreads();
     for (int I = 0; I < R; ++I) {
       if (I == r) continue;
       for (int J = 0; J < R; ++J) {
         if (J == r) continue;
-        product64<EAGER>(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m, sm.prod);
+        product64_lazy(D, ld, P, I * T, J * T, base, min(T, n - I * T), min(T, n - J * T), m, sm.prod);
       }
     }
   }
@@ -636,7 +582,7 @@ __device__ __forceinline__ void persistent_body(float *__restrict__ Dp, int32_t 
     else if (variant == 1 || variant == 2)
       solve_graph_pipe_f32<true>(D, P, n, sm);
     else
-      solve_graph_f32<false>(D, P, n, sm);
+      solve_graph_lazy_f32(D, P, n, sm);
   }
 }
 
