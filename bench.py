@@ -222,7 +222,7 @@ def workload_config(n: int, world: int, dtype: str = "f32") -> dict:
     return {"workload": f"blocked FW, dense directed graph n={n}, p=0.5, int weights U[1,100], "
                         f"{prec} D + int32 P",
             "n": n, "edge_prob": 0.5, "path_matrix": True,
-            "l2": "inputs > L2 (D restored from a resident copy each step)",
+            "l2": "inputs > L2, D restored each step",
             "parallelism": f"{world} independent graph(s), one per GPU"}
 
 
@@ -741,8 +741,8 @@ def run_ours(args):
         # CPU baseline: the oracle as it stands, bounded prefix of the same graph
         rate, k, thr, tcpu = oracle_partial_rate(Wh.numpy(), args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"first {k} outer k iterations of classic FW (Algorithm 1, FP32 + P) on the "
-                                          f"n={n} graph, {tcpu:.1f} s; prefix rate (early k improve more entries)"}
+                                "sample": f"classic FW (FP32 + P), first {k} of {n} outer k, {tcpu:.1f} s: a prefix "
+                                          f"rate (early k write more)"}
         if args.cpu_full:
             details["cpu_full_runs"] = oracle_full_runs(args.cpu_full)
         for key, val in details.items():  # long records first, one line each
@@ -752,8 +752,9 @@ def run_ours(args):
         del W, D, P
     if rank == 0:
         print("# detail " + json.dumps({"roofline": line["roofline"], "phase_time_ms": line.pop("phase_time_ms"),
-                                        "device": line.pop("device")}), flush=True)
-        print(json.dumps(compact_line(line)), flush=True)
+                                        "device": line.pop("device"),
+                                        "e2e_parts_ms": (line.get("e2e") or {}).get("parts_ms")}), flush=True)
+        print(json.dumps(compact_line(line), separators=(",", ":")), flush=True)
     barrier(world)
 
 
@@ -771,6 +772,8 @@ def compact_line(line):
     if out.get("energy"):
         out["energy"] = {k: r4(v) for k, v in out["energy"].items() if k != "relax_per_joule"}
     out["ms_per_step"] = round(out["ms_per_step"], 3)
+    if out.get("e2e"):
+        out["e2e"] = {k: r4(v) for k, v in out["e2e"].items() if k != "parts_ms"}
     return out
 
 
@@ -810,12 +813,6 @@ def summary_of(details, line):
     if fb:
         out["fwd_bwd_ms"] = round(fb["fwd_bwd_ms"], 3)
         out["fwd_bwd_per_graph_ms"] = round(fb["per_graph_path"]["fwd_bwd_ms"], 2)
-    s64 = details.get("sweep_f64")
-    if s64:
-        out["sweep_f64_relax_per_s"] = {str(p["n"]): float("%.4g" % p["relax_per_s"]) for p in s64["points"]}
-    sw = details.get("sweep")
-    if sw:
-        out["sweep_relax_per_s"] = {str(p["n"]): float("%.4g" % p["with_path"]["relax_per_s"]) for p in sw["points"]}
     en = line.get("energy")
     if en:
         out["eq1_gflops_per_w"] = round(en["eq1_gflops_per_w"], 2)

@@ -83,3 +83,44 @@ def test_recorded_profiler_captures_stay_small():
         if not only_duration:
             count = re.search(r"\s-c\s+(\d+)", cmd)
             assert count and int(count.group(1)) <= 3, (name, cmd)
+
+
+def test_final_line_stays_short_and_carries_every_headline():
+    """The last JSON line (the one a log tail keeps) holds the FP32 value, the
+    roofline, e2e, the CPU baseline and the summary of the FP64, batched (with
+    and without P) and forward+backward numbers in under 1.5 KB; the long
+    records (sweeps, per-phase times, e2e parts) go to the detail lines."""
+    import json
+    details = {
+        "fp64": {"value": 1.299e13, "ms": 2708.0, "phase3_frac_of_unit_peak": 0.3209,
+                 "phase3_frac_of_measured_pair_rate": 0.4562, "phase_time_ms": {"x": {"ms": 1.0, "launches": 3}}},
+        "batched": {"graphs_per_s": 183160.2, "ms": 22.363, "relax_per_s": 6.476e12, "frac_of_unit_peak": 0.1608,
+                    "speedup_vs_per_graph": 55.4, "without_path": {"ms": 15.614, "relax_per_s": 9.3e12,
+                                                                   "frac_of_unit_peak": 0.23},
+                    "autotuned_variants": {str(c): {"ms_per_variant": [1.0, 2.0, 3.0]} for c in range(4)}},
+        "fwd_bwd": {"fwd_bwd_ms": 1.198, "per_graph_path": {"fwd_bwd_ms": 72.36}},
+        "sweep": {"points": [{"n": n, "with_path": {"relax_per_s": 1e13}} for n in (4096, 8192, 32768, 65536)]},
+        "sweep_f64": {"points": [{"n": n, "relax_per_s": 5e12} for n in (4096, 8192)]},
+    }
+    line = {"metric": bench.METRIC, "value": 1.557e13, "unit": bench.UNIT, "n_gpus": 1, "steps": 3, "warmup": 3,
+            "ms_per_step": 2261.3361, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": bench.workload_config(32768, 1, "f32"),
+            "roofline": {"bound": "alu", "achieved": 30.95123, "peak": 80.55, "unit": "TFLOP/s", "frac": 0.38421,
+                         "traffic": 5.737e9, "frac_of_measured_pair_rate": 0.5481, "avg_round_ms": 8.812,
+                         "flop_def": "x" * 200, "peak_basis": "y" * 100},
+            "gpu_launches": 3072, "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []},
+            "energy": {"power_w_mean": 542.0, "eq1_gflops_per_w": 57.44, "relax_per_joule": 2.9e10},
+            "e2e": {"value": 1.27e13, "unit": bench.UNIT, "h2d_bytes_per_step": 1 << 32,
+                    "d2h_bytes_per_step": 1 << 33, "parts_ms": {"step_ms": 2765.33, "host_wall_ms": 2765.38}},
+            "cpu_baseline": {"value": 2.0e10, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
+                             "sample": "classic FW (FP32 + P), first 137 of 32768 outer k, 7.3 s: a prefix rate (early k write more)"}}
+    line["summary"] = bench.summary_of(details, line)
+    out = json.dumps(bench.compact_line(line), separators=(",", ":"))
+    assert len(out) < 1500
+    d = json.loads(out)
+    assert set(bench.ROOFLINE_KEYS) >= set(d["roofline"]) and "flop_def" not in d["roofline"]
+    s = d["summary"]
+    assert s["fp64"]["value"] == 1.299e13 and s["batched"]["no_path_ms"] == 15.614
+    assert s["fwd_bwd_ms"] == 1.198 and "parts_ms" not in d["e2e"]
+    for key in ("e2e", "cpu_baseline", "clocks", "gpu_launches"):
+        assert key in d
