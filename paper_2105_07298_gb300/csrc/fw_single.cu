@@ -331,6 +331,40 @@ __global__ void __launch_bounds__(mp32::THREADS, EAGER ? APSP_K3_EAGER_MIN_BLOCK
     };
     unsigned long long b0[4], b1[4];
     load_b(0, b0);
+    if constexpr (EAGER) {
+      // Both k-pairs of a step per output, one compare and one byte permute
+      // per four candidates: the byte keeps the step's first k-pair.
+      auto compute2 = [&](int kp, const unsigned long long (&p0)[4], const unsigned long long (&p1)[4]) {
+        ulonglong2 n0 = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(0, ty)]);
+        ulonglong2 n1 = *reinterpret_cast<const ulonglong2 *>(&Asl[(kp + 1) * T + row_at(0, ty)]);
+#pragma unroll
+        for (int rp = 0; rp < 4; ++rp) {
+          const ulonglong2 c0 = n0, c1 = n1;
+          if (rp < 3) {
+            n0 = *reinterpret_cast<const ulonglong2 *>(&Asl[kp * T + row_at(2 * rp + 2, ty)]);
+            n1 = *reinterpret_cast<const ulonglong2 *>(&Asl[(kp + 1) * T + row_at(2 * rp + 2, ty)]);
+          }
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float &acc_o = acc[2 * rp + h][cc];
+              const float m1 = mp32::min3f_pair(acc_o, h ? c0.y : c0.x, p0[cc]);
+              const float m2 = mp32::min3f_pair(m1, h ? c1.y : c1.x, p1[cc]);
+              if (m2 < acc_o)
+                kid[2 * rp + h] = __byte_perm(kid[2 * rp + h], kbase + kp,
+                                              0x3210 ^ ((0x3210 & (0xF << (4 * cc))) ^ (4 << (4 * cc))));
+              acc_o = m2;
+            }
+        }
+      };
+#pragma unroll 4
+      for (int kp = 0; kp < KP; kp += 2) {
+        load_b(kp + 1, b1);
+        compute2(kp, b0, b1);
+        if (kp + 2 < KP) load_b(kp + 2, b0);
+      }
+    } else {
 // Unrolled by four (measured best of 1, 2, 4 and 8).
 #pragma unroll 4
     for (int kp = 0; kp < KP; kp += 2) {
@@ -338,6 +372,7 @@ __global__ void __launch_bounds__(mp32::THREADS, EAGER ? APSP_K3_EAGER_MIN_BLOCK
       compute(kp, b0);
       if (kp + 2 < KP) load_b(kp + 2, b0);
       compute(kp + 1, b1);
+    }
     }
     __syncthreads();  // stage st fully read
     if (tid == 0 && s + STAGES < nslab) {
@@ -407,9 +442,9 @@ __global__ void __launch_bounds__(mp32::THREADS, EAGER ? APSP_K3_EAGER_MIN_BLOCK
   }
   if (!P) return;
   if constexpr (EAGER) {
-    // The k inside each improved output's last decreasing pair: the lower one
-    // if its candidate equals the new value (the sequential loop keeps the
-    // first k reaching a minimum).
+    // The k inside each improved output's last decreasing step (two k-pairs):
+    // the first whose candidate equals the new value (the sequential loop
+    // keeps the first k reaching a minimum).
 #pragma unroll 1
     for (int t = 0; t < 16; ++t)
 #pragma unroll
@@ -417,8 +452,18 @@ __global__ void __launch_bounds__(mp32::THREADS, EAGER ? APSP_K3_EAGER_MIN_BLOCK
         if (!((flags >> (2 * t + q)) & 1u)) continue;
         const int i = i0 + t, j = j0 + q;
         const int kp = Ks[i * H + j];  // an improved output has one
+        const float g = Cs[i * H + j];
         const float2 c = mp32::sum2(srcA[(int64_t)kp * T + i], srcB[(int64_t)kp * H + j]);
-        P[(int64_t)(baseI + i) * ld + baseJ + j] = baseK + (c.x == Cs[i * H + j] ? 2 * kp : 2 * kp + 1);
+        int k;
+        if (c.x == g) {
+          k = 2 * kp;
+        } else if (c.y == g) {
+          k = 2 * kp + 1;
+        } else {  // the second k-pair of the step
+          const float2 c2 = mp32::sum2(srcA[(int64_t)(kp + 1) * T + i], srcB[(int64_t)(kp + 1) * H + j]);
+          k = c2.x == g ? 2 * kp + 2 : 2 * kp + 3;
+        }
+        P[(int64_t)(baseI + i) * ld + baseJ + j] = baseK + k;
       }
     return;
   }

@@ -180,7 +180,8 @@ struct Smem {
 #endif
 // Rounds that track P in the main loop (EAGER): in the first rounds nearly
 // every output improves, and one compare and one byte permute per k-pair
-// cost less than recomputing every candidate afterwards.
+// (per two k-pairs in the single-graph kernel) cost less than recomputing
+// every candidate afterwards.
 constexpr int kEagerRounds = APSP_K3_EAGER_ROUNDS;
 
 #ifndef APSP_K3_EAGER_MIN_BLOCKS
