@@ -174,6 +174,18 @@ def alu_peak_relax_per_s(sms: int, mhz: float) -> float:
     return 128.0 * sms * mhz * 1e6
 
 
+def eq1_gflops(relax_per_s: float) -> float:
+    """The paper's Eq. 1 rate, GFLOPS = 2 N^3 / (t 10^9): two floating-point
+    operations (the add and the compare) per relaxation."""
+    return 2.0 * relax_per_s / 1e9
+
+
+def gflops_per_watt(gflops: float, watts: float) -> float:
+    """Energy efficiency as the paper's Tables 2 and 3 give it (§4.3): Eq. 1
+    GFLOPS over the platform's power in watts."""
+    return gflops / watts
+
+
 def kernel_source_hash() -> str:
     """Hash of the sources the phase-4 kernel is built from: the shared headers,
     its constants and shared-memory layout (namespace k3 of phases_f32.cuh) and
@@ -694,7 +706,7 @@ def run_ours(args):
         # the paper's Table 3 metric: Eq. 1 GFLOPS (2 per relaxation) per watt of
         # board power sampled during the timed region
         "energy": ({"power_w_mean": clocks["power_w_mean"],
-                    "eq1_gflops_per_w": 2 * value / world / 1e9 / clocks["power_w_mean"],
+                    "eq1_gflops_per_w": gflops_per_watt(eq1_gflops(value / world), clocks["power_w_mean"]),
                     "relax_per_joule": value / world / clocks["power_w_mean"]}
                    if clocks and clocks.get("power_w_mean") else None),
         "device": facts,
