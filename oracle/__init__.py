@@ -34,43 +34,53 @@ _i64 = ctypes.c_int64
 _p = ctypes.c_void_p
 
 
+def compile_library(src: str, out: str) -> str:
+    """Compile a C source with the oracle's flags (gcc, -O2, OpenMP, no fp
+    contraction) into the shared library ``out``."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile fw_oracle.c into liboracle.so (gcc, -O2, OpenMP, no fp contraction)."""
+    """Compile fw_oracle.c into liboracle.so (if missing or older than the source)."""
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_library(_SRC, _LIB_PATH)
+
+
+def load_library(path: str):
+    """Load a build of fw_oracle.c and declare its exported signatures."""
+    L = ctypes.CDLL(path)
+    for name in ("oracle_fw_f64", "oracle_fw_f32"):
+        getattr(L, name).argtypes = [_p, _i64, _p, _i64]
+        getattr(L, name).restype = None
+    for name in ("oracle_bfw_f64", "oracle_bfw_f32"):
+        getattr(L, name).argtypes = [_p, _i64, _i64, _p]
+        getattr(L, name).restype = ctypes.c_int
+    L.oracle_dijkstra_f64.argtypes = [_p, _i64, _i64, _p]
+    L.oracle_dijkstra_rows.argtypes = [_p, ctypes.c_int, _i64, _p, _i64, _p]
+    L.oracle_bellman_ford_f64.argtypes = [_p, _i64, _i64, _p]
+    L.oracle_bellman_ford_f64.restype = ctypes.c_int
+    L.oracle_reconstruct_path.argtypes = [_p, _i64, _i64, _i64, _p, _i64]
+    L.oracle_reconstruct_path.restype = _i64
+    L.oracle_fw_backward_f64.argtypes = [_p, _p, _p, _i64, _p]
+    L.oracle_fw_backward_f64.restype = ctypes.c_int
+    L.oracle_num_threads.restype = ctypes.c_int
+    L.oracle_minplus_rows_f32.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p]
+    L.oracle_minplus_rows_f32.restype = None
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = ctypes.CDLL(_LIB_PATH)
-            for name in ("oracle_fw_f64", "oracle_fw_f32"):
-                getattr(L, name).argtypes = [_p, _i64, _p, _i64]
-                getattr(L, name).restype = None
-            for name in ("oracle_bfw_f64", "oracle_bfw_f32"):
-                getattr(L, name).argtypes = [_p, _i64, _i64, _p]
-                getattr(L, name).restype = ctypes.c_int
-            L.oracle_dijkstra_f64.argtypes = [_p, _i64, _i64, _p]
-            L.oracle_dijkstra_rows.argtypes = [_p, ctypes.c_int, _i64, _p, _i64, _p]
-            L.oracle_bellman_ford_f64.argtypes = [_p, _i64, _i64, _p]
-            L.oracle_bellman_ford_f64.restype = ctypes.c_int
-            L.oracle_reconstruct_path.argtypes = [_p, _i64, _i64, _i64, _p, _i64]
-            L.oracle_reconstruct_path.restype = _i64
-            L.oracle_fw_backward_f64.argtypes = [_p, _p, _p, _i64, _p]
-            L.oracle_fw_backward_f64.restype = ctypes.c_int
-            L.oracle_num_threads.restype = ctypes.c_int
-            L.oracle_minplus_rows_f32.argtypes = [_p, _i64, _i64, _p, _i64, _i64, _p]
-            L.oracle_minplus_rows_f32.restype = None
-            _lib = L
+            _lib = load_library(build())
     return _lib
 
 
