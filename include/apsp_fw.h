@@ -257,7 +257,6 @@ int apsp_fw_backward_packed_f32(const float *d_grad_dist, const int32_t *d_path,
                                 float *d_grad_w, const int32_t *d_n, const int64_t *d_off,
                                 int32_t num_graphs, int32_t *d_status, void *stream);
 
-
 /* ------------------------------------------------------------------------
  * Phase timing (a measurement hook; the paper times whole runs only, §4.1).
  * apsp_profile_enable(1) clears earlier records and starts bracketing every
@@ -270,6 +269,16 @@ int apsp_fw_backward_packed_f32(const float *d_grad_dist, const int32_t *d_path,
  * graph is being captured.
  * ---------------------------------------------------------------------- */
 int apsp_profile_enable(int on);
+int apsp_profile_collect(double *ms, int64_t *launches);
+
+/* The same records one by one, in launch order (per-round timing: the r-th
+ * phase-4 record is round r of the last solve when one solve was recorded).
+ * Waits for the recorded events; writes min(cap, records) entries to
+ * phase[] (index as above) and ms[] (device time of that launch), and the
+ * number of records to *count.  phase and ms may be NULL when cap is 0.
+ * Returns APSP_EINVAL for a NULL count, a negative cap, or NULL arrays with
+ * cap > 0. */
+int apsp_profile_records(int32_t *phase, float *ms, int64_t cap, int64_t *count);
 
 /* Measured ceiling of the relaxation on this GPU (a measurement hook; the
  * paper quotes datasheet peaks only, Table 1): runs the inner-loop
@@ -309,16 +318,6 @@ int apsp_wait_timeout_selftest(uint32_t polls, void *stream);
  * word of the library (calls from several host threads are serialised by a
  * lock); allocates nothing; not for use while `stream` is being captured. */
 int apsp_check_negative_cycle(const void *d_dist, int elem_bytes, int64_t n, int64_t ld, void *stream);
-int apsp_profile_collect(double *ms, int64_t *launches);
-
-/* The same records one by one, in launch order (per-round timing: the r-th
- * phase-4 record is round r of the last solve when one solve was recorded).
- * Waits for the recorded events; writes min(cap, records) entries to
- * phase[] (index as above) and ms[] (device time of that launch), and the
- * number of records to *count.  phase and ms may be NULL when cap is 0.
- * Returns APSP_EINVAL for a NULL count, a negative cap, or NULL arrays with
- * cap > 0. */
-int apsp_profile_records(int32_t *phase, float *ms, int64_t cap, int64_t *count);
 
 #ifdef __cplusplus
 }
