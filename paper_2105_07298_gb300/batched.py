@@ -27,6 +27,25 @@ def _host_arrays(sizes, offsets):
     return n, off
 
 
+def _layout_numel(n, off) -> int:
+    """Elements the packed layout spans (end of its last-ending graph)."""
+    return int(np.max(off + n.astype(np.int64) ** 2)) if len(n) else 0
+
+
+def _check_buffers(dist, path, need: int):
+    """The packed buffers a batched call writes: ``dist`` a contiguous CUDA
+    float32 tensor of at least ``need`` elements; ``path`` (optional) a
+    contiguous int32 tensor on the same device, as large as ``dist``."""
+    import torch
+    if dist.dtype != torch.float32 or not dist.is_cuda or not dist.is_contiguous():
+        raise TypeError("dist must be a contiguous CUDA float32 tensor")
+    if path is not None and (path.dtype != torch.int32 or not path.is_cuda or path.device != dist.device
+                             or not path.is_contiguous() or path.numel() < dist.numel()):
+        raise TypeError("path must be a contiguous int32 tensor on dist's device, as large as dist")
+    if dist.numel() < need:
+        raise ValueError(f"dist has {dist.numel()} elements, layout needs {need}")
+
+
 def packed_offsets(sizes):
     """Element offsets for graphs packed back to back, each rounded up to 4 elements."""
     return _host_arrays(sizes, None)[1]
@@ -51,18 +70,8 @@ class BatchedPlan:
 
     def run(self, dist, path=None, stream=None):
         """Solve every graph in the packed FP32 buffer ``dist`` (and write ``path``) in place."""
-        import torch
         from . import _check, _stream_ptr
-        if dist.dtype != torch.float32 or not dist.is_cuda or not dist.is_contiguous():
-            raise TypeError("dist must be a contiguous CUDA float32 tensor")
-        if path is not None and (path.dtype != torch.int32 or not path.is_contiguous()
-                                 or path.numel() < dist.numel()):
-            raise TypeError("path must be a contiguous int32 tensor as large as dist")
-        need = int(self.offsets.max(initial=0) + 0) if len(self.sizes) else 0
-        if len(self.sizes):
-            need = int(np.max(self.offsets + self.sizes.astype(np.int64) ** 2))
-        if dist.numel() < need:
-            raise ValueError(f"dist has {dist.numel()} elements, layout needs {need}")
+        _check_buffers(dist, path, _layout_numel(self.sizes, self.offsets))
         _check(self._lib.apsp_fw_batched_run_f32(
             self._h, ctypes.c_void_p(dist.data_ptr()),
             ctypes.c_void_p(path.data_ptr()) if path is not None else None, _stream_ptr(stream)),
@@ -83,13 +92,9 @@ class BatchedPlan:
 
 def apsp_fw_batched_f32(dist, sizes, offsets=None, path=None, stream=None):
     """One-shot batched solve (plan, run and free in one call)."""
-    import torch
     from . import load, _check, _stream_ptr
     n, off = _host_arrays(sizes, offsets)
-    if dist.dtype != torch.float32 or not dist.is_cuda or not dist.is_contiguous():
-        raise TypeError("dist must be a contiguous CUDA float32 tensor")
-    if len(n) and dist.numel() < int(np.max(off + n.astype(np.int64) ** 2)):
-        raise ValueError("dist is smaller than the layout")
+    _check_buffers(dist, path, _layout_numel(n, off))
     _check(load().apsp_fw_batched_f32(
         ctypes.c_void_p(dist.data_ptr()), ctypes.c_void_p(path.data_ptr()) if path is not None else None,
         n.ctypes.data_as(ctypes.c_void_p), off.ctypes.data_as(ctypes.c_void_p), len(n),
