@@ -82,3 +82,39 @@ def test_phase3_relaxation_count_is_the_algorithmic_work():
         m = min(T, n - r * T)
         phase123 += m ** 3 + 2 * m * m * (n - m)
     assert phase4 + phase123 == pytest.approx(n ** 3)
+
+
+def _reference_worker(rank, world, port, path):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    import argparse
+    import contextlib
+    args = argparse.Namespace(n=192, steps=2, warmup=1, dtype="f32", ref_step_seconds=0.2)
+    with open(f"{path}.{rank}", "w") as f, contextlib.redirect_stdout(f):
+        bench.run_reference(args)
+
+
+def test_reference_arm_under_two_ranks_prints_one_line_from_rank_0(tmp_path):
+    """The CPU reference arm as torchrun launches it for N > 1: rank 0 alone
+    times the oracle and prints the one JSON line; the other rank exits 0
+    without work or output."""
+    import json
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    path = str(tmp_path / "out")
+    procs = [ctx.Process(target=_reference_worker, args=(r, 2, port, path)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+        assert p.exitcode == 0
+    lines0 = open(f"{path}.0").read().strip().splitlines()
+    assert open(f"{path}.1").read() == ""
+    assert len(lines0) == 1
+    line = json.loads(lines0[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 2
+    assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC and line["higher_is_better"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"] > 0
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"] == bench.workload_config(192, 2)
