@@ -124,3 +124,16 @@ def test_final_line_stays_short_and_carries_every_headline():
     assert s["fwd_bwd_ms"] == 1.198 and "parts_ms" not in d["e2e"]
     for key in ("e2e", "cpu_baseline", "clocks", "gpu_launches"):
         assert key in d
+
+
+def test_cpu_baseline_sample_is_a_measured_prefix():
+    """The CPU baseline times a prefix of the oracle's outer k loop: k between
+    the probe and n, a positive rate n^2 k / t, the oracle's thread count."""
+    import graphgen
+    import oracle
+    W = graphgen.dense_graph(256, 0.5, bench.SEED)
+    rate, k, threads, t = bench.oracle_partial_rate(W, 0.05, probe_k=8)
+    assert 8 <= k <= 256 and t > 0 and threads == oracle.num_threads() >= 1
+    assert rate == pytest.approx(k * 256.0 ** 2 / t)
+    runs = bench.oracle_full_runs([128])
+    assert runs[0]["n"] == 128 and runs[0]["relax_per_s"] == pytest.approx(128.0 ** 3 / runs[0]["s"])
