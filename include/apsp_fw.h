@@ -53,7 +53,7 @@ typedef enum {
   APSP_EINVAL = 1,        /* bad argument (null pointer, n < 0, ld < n, ...) */
   APSP_ECUDA = 2,         /* a CUDA call or launch failed */
   APSP_ENOMEM = 3,        /* device scratch allocation failed */
-  APSP_EUNSUPPORTED = 4,  /* size or feature outside what this build supports */
+  APSP_EUNSUPPORTED = 4,  /* size or feature outside what the library supports */
   APSP_ETOODEEP = 5,      /* backward: a path's recursion exceeded the walk stack */
   APSP_ENEGCYCLE = 6,     /* apsp_check_negative_cycle: some D[i][i] < 0 */
   APSP_ETIMEOUT = 7       /* a kernel's bounded wait for an asynchronous copy ran out */
