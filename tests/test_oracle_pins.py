@@ -219,6 +219,38 @@ def test_bfw_real_weights_close_to_fp64():
     assert oracle.check_paths(W, Db, Pb, rtol=1e-5) == 0
 
 
+@pytest.mark.parametrize("TB", [None, 16, 128])
+def test_fp32_error_within_the_rounding_bound_of_its_paths(TB):
+    """FP32 against FP64 on the same (float) weights, entry by entry.  Rounding
+    is monotone and a positive sum of L terms rounded L - 1 times lies within
+    (1 -+ u)^(L-1) of the exact sum (u = 2^-24).  The FP32 run evaluates
+    (a composition of rounded sub-results no larger than) the FP64 optimum's
+    path p*, so D32 <= D64 (1 + u)^(|p*| - 1); and D32 is the rounded sum of the
+    path q its own P encodes, whose exact sum is >= D64, so
+    D32 >= D64 (1 - u)^(|q| - 1).  Much tighter than the 1e-5 tolerance: a
+    double rounding, a lost term or a wrong operand would break it."""
+    n = 120
+    W = _rand_graph(n, 0.4, 61, weights="real", lo=0.5, hi=2.0, dtype=np.float32)
+    D32, P32 = oracle.fw(W) if TB is None else oracle.bfw(W, TB)
+    D64, P64 = oracle.fw(W.astype(np.float64))
+    u, eps = 2.0 ** -24, n * 2.0 ** -52
+    checked = 0
+    for i in range(n):
+        for j in range(n):
+            d64 = D64[i, j]
+            if i == j or not np.isfinite(d64):
+                assert D32[i, j] == d64
+                continue
+            lq = len(oracle.reconstruct_path(P32, i, j)) - 1
+            lp = len(oracle.reconstruct_path(P64, i, j)) - 1
+            d32 = float(D32[i, j])
+            assert d64 * (1 - u) ** (lq - 1) * (1 - eps) <= d32 <= d64 * (1 + u) ** (lp - 1) * (1 + eps), \
+                (i, j, d32, d64, lq, lp)
+            checked += 1
+    assert checked > n * n // 2
+    assert np.any(D32.astype(np.float64) != D64)  # the bound is exercised, not trivially equal
+
+
 def test_bfw_rejects_bad_block():
     with pytest.raises(ValueError):
         oracle.bfw(np.zeros((3, 3)), 0)
