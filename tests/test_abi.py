@@ -4,7 +4,6 @@ import ctypes
 import os
 import re
 
-
 import paper_2105_07298_gb300 as apsp
 from paper_2105_07298_gb300 import build as apsp_build
 
