@@ -80,3 +80,27 @@ def test_new_entry_points_reject_bad_arguments_without_gpu():
     for st in range(8):
         assert L.apsp_status_string(st).startswith(b"APSP_")
     assert L.apsp_status_string(7) == b"APSP_ETIMEOUT: a kernel's bounded wait for an asynchronous copy ran out"
+
+
+def test_batched_entry_points_reject_bad_layouts_without_gpu():
+    """The batched entry points check sizes and offsets on the host before any
+    CUDA call: size 0 or negative, a size above the batched limit, an offset
+    that is negative or not 16-byte aligned, and (no-allocation form) more
+    graphs than its fixed work list holds."""
+    L = apsp.load()
+
+    def call(fn, sizes, offs):
+        n = (ctypes.c_int32 * len(sizes))(*sizes)
+        o = (ctypes.c_int64 * len(offs))(*offs)
+        return getattr(L, fn)(None, None, n, o, len(sizes), None)
+
+    for fn in ("apsp_fw_batched_f32", "apsp_fw_batched_f32_noalloc"):
+        assert call(fn, [4, 0], [0, 16]) == apsp.APSP_EINVAL
+        assert call(fn, [4, -3], [0, 16]) == apsp.APSP_EINVAL
+        assert call(fn, [4, 1025], [0, 16]) == apsp.APSP_EUNSUPPORTED
+        assert call(fn, [4, 4], [0, 18]) == apsp.APSP_EINVAL      # offset not a multiple of 4
+        assert call(fn, [4, 4], [0, -16]) == apsp.APSP_EINVAL
+        assert getattr(L, fn)(None, None, None, None, 0, None) == apsp.APSP_OK  # empty batch: no-op
+        assert getattr(L, fn)(None, None, None, None, -1, None) == apsp.APSP_EINVAL
+    big = 65537
+    assert call("apsp_fw_batched_f32_noalloc", [2] * big, [4 * g for g in range(big)]) == apsp.APSP_EUNSUPPORTED
