@@ -104,3 +104,23 @@ def test_batched_entry_points_reject_bad_layouts_without_gpu():
         assert getattr(L, fn)(None, None, None, None, -1, None) == apsp.APSP_EINVAL
     big = 65537
     assert call("apsp_fw_batched_f32_noalloc", [2] * big, [4 * g for g in range(big)]) == apsp.APSP_EUNSUPPORTED
+
+
+def test_single_graph_and_backward_arguments_without_gpu():
+    """int32 entry and the uniform backward entry check their arguments before
+    any CUDA call (n out of range, ld < n, null buffers, stride too short)."""
+    L = apsp.load()
+    for fn in (L.apsp_fw_f32, L.apsp_fw_f64, L.apsp_fw_i32):
+        assert fn(None, 0, 0, None, None) == apsp.APSP_OK                 # n = 0: no-op
+        assert fn(None, -1, 4, None, None) == apsp.APSP_EINVAL
+        assert fn(None, (1 << 18) + 1, (1 << 18) + 1, None, None) == apsp.APSP_EINVAL
+        assert fn(None, 8, 8, None, None) == apsp.APSP_EINVAL             # null matrix
+        assert fn(ctypes.c_void_p(16), 8, 7, None, None) == apsp.APSP_EINVAL  # ld < n
+    bw = L.apsp_fw_backward_f32
+    p = ctypes.c_void_p(16)
+    assert bw(None, None, None, None, 0, 0, 1, 0, None, None) == apsp.APSP_OK   # nothing to do
+    assert bw(None, None, None, None, -1, 4, 1, 16, None, None) == apsp.APSP_EINVAL
+    assert bw(None, None, None, None, 4, 4, -1, 16, None, None) == apsp.APSP_EINVAL
+    assert bw(p, p, None, p, 4, 4, 1, 16, None, None) == apsp.APSP_EINVAL       # null D
+    assert bw(p, p, p, p, 4, 3, 1, 16, None, None) == apsp.APSP_EINVAL          # ld < n
+    assert bw(p, p, p, p, 4, 4, 2, 15, None, None) == apsp.APSP_EINVAL          # graphs would overlap
