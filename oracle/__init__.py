@@ -13,7 +13,7 @@ Readings of the paper used here:
   * strict "<" in Algorithm 1 (the printed ">=" makes path reconstruction loop
     forever at k = j);
   * P = -1 marks "no intermediate vertex" (direct edge, i == j or unreachable);
-  * IEEE +inf for "no path" (§2.2 footnote says "largest positive value").
+  * IEEE +inf for "no path" (§2.2's footnote uses the maximum positive number).
 """
 from __future__ import annotations
 

@@ -12,8 +12,8 @@
  * Conventions (readings of points the paper leaves open):
  *   - D is a dense n x n row-major matrix; D[i*n+j] is the length of the
  *     directed edge i -> j, +inf where there is none, 0 on the diagonal
- *     (§2.2 "FW Algorithm": "infinite" distance for no path; IEEE +inf is used
- *     so that inf + x = inf and every comparison is exact).
+ *     (§2.2 "FW Algorithm": a missing path has infinite distance; IEEE +inf
+ *     is used so that inf + x = inf and every comparison is exact).
  *   - Algorithm 1 prints the test "D[i][j] >= D[i][k] + D[k][j]".  Taken with
  *     ">=", the step k = j (D[j][j] = 0) would set P[i][j] = j for every
  *     reachable pair and path reconstruction would never end.  The oracle uses
