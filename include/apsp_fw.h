@@ -4,7 +4,7 @@
  *
  * Method: Costanzo et al., "Comparison of HPC Architectures for Computing
  * All-Pairs Shortest Paths. Intel Xeon Phi KNL vs NVIDIA Pascal"
- * (arXiv 2105.07298), §2.2: Floyd-Warshall (Algorithm 1) computed by blocks
+ * (arXiv 2105.07298), §2.2: Floyd-Warshall (Algorithm 1) evaluated block by block
  * (the blocked FW of §2.2, "Blocked FW Algorithm": TB x TB blocks, R = N/TB
  * rounds of four dependency-ordered phases) and §3.2 (one kernel for phase 1,
  * one for phases 2+3, one for phase 4 per round).
