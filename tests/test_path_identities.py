@@ -15,7 +15,9 @@ ways:
     strict decrease is kept, and inside it the first k whose candidate
     equals the final value is taken.
 FP64 pass 1 tests "x below ru(d)" for a float x and a double d; that equals
-"x below d" (a float below d is below the smallest float >= d).
+"x below d" (a float below d is below the smallest float >= d).  The FP64
+path's float bounds bracket every exact sum (lower bounds added rounding down,
+upper bounds rounding up), which is what lets it skip or confirm candidates.
 """
 import math
 import random
@@ -125,3 +127,52 @@ def test_eager_chunks_give_the_sequential_path_entry(seed):
     sequential loop's last improvement."""
     for init, cands in _cases(100 + seed, 3000):
         assert eager_chunks(init, cands) == sequential(init, cands)
+
+
+# --------------------------------------------------------------- FP64 interval bounds
+def _down32(x):
+    """Largest float32 <= x (x a Fraction or +-inf)."""
+    from fractions import Fraction
+    if x in (math.inf, -math.inf):
+        return np.float32(x)
+    f = np.float32(float(x))
+    if math.isinf(f) and f < 0:  # below every finite float
+        return f
+    while math.isinf(f) or Fraction(float(f)) > x:
+        f = np.nextafter(f, np.float32(-np.inf))
+    while True:
+        g = np.nextafter(f, np.float32(np.inf))
+        if math.isinf(g) or Fraction(float(g)) > x:
+            return f
+        f = g
+
+
+def _up32(x):
+    """Smallest float32 >= x (x a Fraction)."""
+    return -_down32(-x)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_fp64_interval_sums_bracket_the_exact_sum(seed):
+    """Each FP64 value is carried as float bounds [rd(d), ru(d)].  The main
+    loop adds lower bounds rounding down, the confirmation adds upper bounds
+    rounding up; the exact sum always lies between, so (a) "lower sum >= ru(old)"
+    proves no FP64 candidate beats old, and (b) equal bounds prove the sum exact."""
+    from fractions import Fraction
+    rng = random.Random(seed)
+    for _ in range(4000):
+        a = rng.choice([rng.uniform(0, 1e3), rng.uniform(0, 1) * 2.0 ** rng.randint(-60, 60),
+                        float(rng.randint(1, 1 << 30)), rng.uniform(0, 1e3) + 2.0 ** -40])
+        b = rng.choice([rng.uniform(0, 1e3), rng.uniform(0, 1) * 2.0 ** rng.randint(-60, 60),
+                        float(rng.randint(1, 1 << 30))])
+        A, B = Fraction(a), Fraction(b)
+        la, ha, lb, hb = _down32(A), _up32(A), _down32(B), _up32(B)
+        lo = _down32(Fraction(float(la)) + Fraction(float(lb)))   # add.rm of the lower bounds
+        hi = _up32(Fraction(float(ha)) + Fraction(float(hb)))   # add.rp of the upper bounds
+        exact = A + B
+        assert Fraction(float(lo)) <= exact <= Fraction(float(hi)), (a, b)
+        if lo == hi:
+            assert exact == Fraction(float(lo))
+        old = rng.choice([a + b, (a + b) * (1 + 1e-12), (a + b) * (1 - 1e-12), rng.uniform(0, 2e3)])
+        if float(lo) >= float(_up32(Fraction(old))):
+            assert not (a + b < old), (a, b, old)     # the filter never drops an improvement
