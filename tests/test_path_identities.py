@@ -138,8 +138,10 @@ def _down32(x):
     f = np.float32(float(x))
     if math.isinf(f) and f < 0:  # below every finite float
         return f
-    while math.isinf(f) or Fraction(float(f)) > x:
+    while (math.isinf(f) and f > 0) or (math.isfinite(f) and Fraction(float(f)) > x):
         f = np.nextafter(f, np.float32(-np.inf))
+    if math.isinf(f):  # stepped below the most negative float
+        return f
     while True:
         g = np.nextafter(f, np.float32(np.inf))
         if math.isinf(g) or Fraction(float(g)) > x:
